@@ -1,0 +1,146 @@
+"""Plain CPU oracle for exact Gauss-Jordan elimination over Z/pZ.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may use this module; the library itself
+never does.  It shares no code with the CUDA path.
+
+The arithmetic lives in ``oracle.c`` (uint64 ``%`` reductions, Fermat
+inverses, lowest-index nonzero pivots); this module compiles it with gcc on
+first use and wraps it with ctypes.  Every function follows paper section
+3.2 (the elimination loop) or section 5 (reading solutions, null spaces and
+rank factorisations off the RREF), cited where it is defined.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain gcc, no arch flags)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+           "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        # ORACLE_LIB lets the mutation test load a deliberately broken build
+        path = os.environ.get("ORACLE_LIB") or build()
+        lib = ctypes.CDLL(path)
+        i64, u32, i32p = ctypes.c_int64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)
+        vp = ctypes.c_void_p
+        lib.oracle_rref.argtypes = [vp, i64, i64, i64, u32, i64, i64, ctypes.c_int,
+                                    i32p, i32p, ctypes.POINTER(ctypes.c_uint32)]
+        lib.oracle_rref.restype = ctypes.c_int
+        lib.oracle_solve.argtypes = [vp, i64, i64, i64, i64, u32, ctypes.c_int,
+                                     vp, i64, vp, i32p, i32p]
+        lib.oracle_solve.restype = ctypes.c_int
+        lib.oracle_inverse.argtypes = [u32, u32]
+        lib.oracle_inverse.restype = u32
+        _lib = lib
+        return lib
+
+
+def _as_matrix(A) -> np.ndarray:
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.uint32))
+    if A.ndim != 2:
+        raise ValueError("expected a 2-D matrix")
+    return A
+
+
+def inverse(h: int, p: int) -> int:
+    """h^(p-2) mod p (Fermat); the pivot inverse of section 3.2."""
+    return int(_load().oracle_inverse(int(h), int(p)))
+
+
+def rref(A, p: int, col_limit: int | None = None, max_pivots: int = -1,
+         nthreads: int = 1):
+    """Reduced row-echelon form of A over Z/pZ (paper section 3.2).
+
+    Returns (R, rank, pivots, det) where R has A's shape with zero rows at the
+    bottom, pivots is an int32 array of length rank, and det is
+    (-1)^swaps * (product of the heads before scaling) -- det(A) for square A
+    searched over all columns, 0 when the rank is short.  Pivot search is
+    limited to columns [0, col_limit); max_pivots >= 0 stops early (a bounded
+    sample used only for timing).
+    """
+    R = _as_matrix(A).copy()
+    m, n = R.shape
+    if col_limit is None:
+        col_limit = n
+    piv = np.full(max(min(m, n), 1), -1, dtype=np.int32)
+    rank = ctypes.c_int32(0)
+    det = ctypes.c_uint32(0)
+    rc = _load().oracle_rref(R.ctypes.data, m, n, n, p, col_limit, max_pivots, nthreads,
+                             ctypes.byref(rank), piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                             ctypes.byref(det))
+    if rc != 0:
+        raise ValueError("oracle_rref rejected its arguments")
+    return R, int(rank.value), piv[: rank.value].copy(), int(det.value)
+
+
+def solve(A, B, p: int, nthreads: int = 1):
+    """Particular solution of A X = B over Z/pZ (paper section 5.2).
+
+    Pivots are restricted to A's columns; right-hand side j is consistent iff
+    rank(A) == rank(A | b_j).  Free variables are set to zero; inconsistent
+    columns of X are zero.  Returns (X, consistent, rank, pivots, reduced
+    augmented matrix).
+    """
+    A = _as_matrix(A)
+    B = _as_matrix(B)
+    m, nA = A.shape
+    if B.shape[0] != m:
+        raise ValueError("A and B need the same number of rows")
+    k = B.shape[1]
+    M = np.ascontiguousarray(np.concatenate([A, B], axis=1))
+    X = np.zeros((max(nA, 1), max(k, 1)), dtype=np.uint32)
+    cons = np.zeros(max(k, 1), dtype=np.uint8)
+    piv = np.full(max(min(m, nA + k), 1), -1, dtype=np.int32)
+    rank = ctypes.c_int32(0)
+    rc = _load().oracle_solve(M.ctypes.data, m, nA, k, nA + k, p, nthreads,
+                              X.ctypes.data, X.shape[1], cons.ctypes.data,
+                              ctypes.byref(rank),
+                              piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc != 0:
+        raise ValueError("oracle_solve rejected its arguments")
+    return (X[:nA, :k].copy(), cons[:k].astype(bool), int(rank.value),
+            piv[: rank.value].copy(), M)
+
+
+def null_space(R: np.ndarray, pivots: np.ndarray, p: int) -> np.ndarray:
+    """Canonical null-space basis read off an RREF (paper section 5.1).
+
+    The non-pivot columns are the free variables; their coefficients form
+    minus the identity.  Returns K (n x (n - rank)) with A K = 0 mod p.
+    """
+    R = np.asarray(R, dtype=np.uint64)
+    n = R.shape[1]
+    piv = [int(c) for c in pivots]
+    free = [c for c in range(n) if c not in set(piv)]
+    K = np.zeros((n, len(free)), dtype=np.uint64)
+    for f_idx, f in enumerate(free):
+        K[f, f_idx] = (p - 1) % p
+        for t, c in enumerate(piv):
+            K[c, f_idx] = R[t, f]
+    return K.astype(np.uint32)

@@ -1,0 +1,228 @@
+/*
+ * oracle.c -- the plain, slow CPU reference for exact Gauss-Jordan elimination
+ * over the prime field Z/pZ.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library's product path may call,
+ * link or load this file: only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg use it.  It shares no code, header, table or
+ * constant with the CUDA path.
+ *
+ * What it computes (paper section 3.2, "Gaussian elimination on GPUs"):
+ * partially pivoted row reduction to the reduced row-echelon form (RREF),
+ * looping over the columns one at a time ("Looping"), searching the current
+ * column for a usable pivot ("Pivoting": over a finite field any nonzero
+ * entry will do, and the RREF does not depend on which one is taken -- this
+ * oracle takes the lowest-index nonzero row), swapping it into place,
+ * scaling the pivot row so the head becomes 1 ("Conditional Rescale"), and
+ * subtracting multiples of the pivot row from EVERY other row, above and
+ * below, so the pivot column becomes a unit vector ("Row reduce"); the row
+ * counter advances only when the head was nonzero ("Increment counters").
+ * The output keeps the input shape, zero rows at the bottom (section 2.3).
+ *
+ * Arithmetic: entries are canonical residues in [0, p), p an odd prime below
+ * 2^31.  Every product is formed in uint64_t (< 2^62) and reduced with the C
+ * '%' operator -- no Barrett, Montgomery, Shoup or limb tricks.  Inverses are
+ * Fermat's h^(p-2) mod p by square-and-multiply.
+ *
+ * Threads: the row updates of one pivot step are independent of one another;
+ * with nthreads > 1 each thread owns a contiguous range of rows and the
+ * threads meet at a barrier after the pivot step and after the updates.  The
+ * arithmetic is identical for every thread count.
+ *
+ * Parity pins: every function here is pinned in tests/test_oracle_pins.py to
+ * facts fixed by the mathematics (RREF of a matrix built from a known RREF,
+ * brute-force rank over all minors, brute-force null spaces and solution
+ * sets for tiny p, closed-form Vandermonde and L*D*U determinants,
+ * polynomial interpolation).
+ */
+#define _POSIX_C_SOURCE 200809L
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+/* h^e mod p by binary exponentiation; uint64 products of residues < 2^62. */
+static uint64_t oracle_powmod(uint64_t h, uint64_t e, uint64_t p) {
+    uint64_t result = 1 % p;
+    h %= p;
+    while (e) {
+        if (e & 1) result = (result * h) % p;
+        h = (h * h) % p;
+        e >>= 1;
+    }
+    return result;
+}
+
+/* Fermat's little theorem: h^(p-1) = 1 for h != 0, so h^(p-2) = 1/h. */
+uint32_t oracle_inverse(uint32_t h, uint32_t p) {
+    return (uint32_t)oracle_powmod(h, (uint64_t)p - 2, p);
+}
+
+typedef struct {
+    uint32_t *A;
+    int64_t m, n, ld;
+    uint64_t p;
+    int64_t col_limit;    /* pivots are searched in columns [0, col_limit) */
+    int64_t max_pivots;   /* stop after this many pivots (< 0: no limit) */
+    int nthreads;
+    pthread_barrier_t bar;
+    /* state written by thread 0 between barriers */
+    int64_t r;            /* current rank = index of the next pivot row */
+    int64_t c;            /* current column */
+    int found;            /* the current column has a nonzero head */
+    int done;
+    int32_t *pivots;
+    uint64_t det_sign_neg; /* parity of row swaps */
+    uint64_t det_prod;     /* product of the heads before scaling */
+} oracle_ctx;
+
+typedef struct { oracle_ctx *C; int tid; } oracle_arg;
+
+/* Pivot step for column c (section 3.2, "Pivoting" and "Conditional
+ * Rescale"): find the lowest row q >= r with A[q][c] != 0, swap rows q and r,
+ * multiply row r by the inverse of its head. */
+static void oracle_pivot_step(oracle_ctx *C) {
+    const int64_t n = C->n, ld = C->ld, c = C->c, r = C->r;
+    const uint64_t p = C->p;
+    uint32_t *A = C->A;
+    int64_t q = -1;
+    for (int64_t i = r; i < C->m; i++) {
+        if (A[i * ld + c] != 0) { q = i; break; }
+    }
+    if (q < 0) { C->found = 0; return; }
+    C->found = 1;
+    if (q != r) {
+        for (int64_t j = 0; j < n; j++) {
+            uint32_t t = A[q * ld + j];
+            A[q * ld + j] = A[r * ld + j];
+            A[r * ld + j] = t;
+        }
+        C->det_sign_neg ^= 1;
+    }
+    uint64_t h = A[r * ld + c];
+    C->det_prod = (C->det_prod * h) % p;
+    uint64_t hinv = oracle_inverse((uint32_t)h, (uint32_t)p);
+    for (int64_t j = c; j < n; j++)
+        A[r * ld + j] = (uint32_t)(((uint64_t)A[r * ld + j] * hinv) % p);
+}
+
+/* Row update for rows [lo, hi) (section 3.2, "Row reduce"): every row i other
+ * than the pivot row with a nonzero entry f in the pivot column becomes
+ * row_i - f * row_r; columns left of c are zero in row r and are skipped. */
+static void oracle_update_rows(oracle_ctx *C, int64_t lo, int64_t hi) {
+    const int64_t n = C->n, ld = C->ld, c = C->c, r = C->r;
+    const uint64_t p = C->p;
+    uint32_t *A = C->A;
+    const uint32_t *prow = A + r * ld;
+    for (int64_t i = lo; i < hi; i++) {
+        if (i == r) continue;
+        uint32_t *row = A + i * ld;
+        uint64_t f = row[c];
+        if (f == 0) continue;
+        uint64_t negf = p - f;
+        for (int64_t j = c; j < n; j++)
+            row[j] = (uint32_t)(((uint64_t)row[j] + negf * (uint64_t)prow[j]) % p);
+    }
+}
+
+static void *oracle_worker(void *argp) {
+    oracle_arg *arg = (oracle_arg *)argp;
+    oracle_ctx *C = arg->C;
+    const int tid = arg->tid, T = C->nthreads;
+    const int64_t m = C->m;
+    const int64_t lo = (m * tid) / T, hi = (m * (tid + 1)) / T;
+    for (;;) {
+        if (tid == 0) {
+            if (C->c >= C->col_limit || C->r >= m ||
+                (C->max_pivots >= 0 && C->r >= C->max_pivots)) {
+                C->done = 1;
+            } else {
+                oracle_pivot_step(C);
+            }
+        }
+        pthread_barrier_wait(&C->bar);
+        if (C->done) break;
+        if (C->found) oracle_update_rows(C, lo, hi);
+        pthread_barrier_wait(&C->bar);
+        if (tid == 0) {   /* section 3.2, "Increment counters" */
+            if (C->found) { C->pivots[C->r] = (int32_t)C->c; C->r++; }
+            C->c++;
+        }
+    }
+    return NULL;
+}
+
+/*
+ * In-place RREF of the m x n row-major matrix A (leading dimension ld).
+ * Pivots are searched in columns [0, col_limit) only; the remaining columns
+ * are carried along (used by oracle_solve).  max_pivots < 0 means run to the
+ * end; otherwise the elimination stops once that many pivots were taken (a
+ * bounded sample for timing).
+ * Outputs: *rank, pivots[0..rank) (the rest of pivots[0..min(m,n)) is set to
+ * -1), *det_out = (-1)^swaps * product of the heads before scaling, which is
+ * det(A) when A is square, col_limit == n and the rank is n (zero if the rank
+ * is short).
+ * Returns 0, or -1 for bad arguments.
+ */
+int oracle_rref(uint32_t *A, int64_t m, int64_t n, int64_t ld, uint32_t p,
+                int64_t col_limit, int64_t max_pivots, int nthreads,
+                int32_t *rank, int32_t *pivots, uint32_t *det_out) {
+    if (m < 0 || n < 0 || ld < n || p < 2 || col_limit < 0 || col_limit > n)
+        return -1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    int64_t mn = m < n ? m : n;
+    for (int64_t i = 0; i < mn; i++) pivots[i] = -1;
+    oracle_ctx C;
+    memset(&C, 0, sizeof C);
+    C.A = A; C.m = m; C.n = n; C.ld = ld; C.p = p;
+    C.col_limit = col_limit; C.max_pivots = max_pivots;
+    C.nthreads = nthreads; C.pivots = pivots;
+    C.det_prod = 1 % p;
+    pthread_barrier_init(&C.bar, NULL, (unsigned)nthreads);
+    oracle_arg args[256];
+    pthread_t th[256];
+    for (int t = 0; t < nthreads; t++) { args[t].C = &C; args[t].tid = t; }
+    for (int t = 1; t < nthreads; t++) pthread_create(&th[t], NULL, oracle_worker, &args[t]);
+    oracle_worker(&args[0]);
+    for (int t = 1; t < nthreads; t++) pthread_join(th[t], NULL);
+    pthread_barrier_destroy(&C.bar);
+    *rank = (int32_t)C.r;
+    if (det_out) {
+        uint64_t d = C.det_prod;
+        if (C.r < mn || m != n) d = 0;
+        if (C.det_sign_neg && d) d = p - d;
+        *det_out = (uint32_t)d;
+    }
+    return 0;
+}
+
+/*
+ * Solve A X = B over Z/pZ (section 5.2, "Solving linear systems"): reduce
+ * the augmented matrix M = [A | B] (m x (nA + k), leading dimension ld,
+ * overwritten) with pivots restricted to A's columns.  Right-hand side j is
+ * consistent iff rank(A) = rank(A | b_j), i.e. iff column j of the reduced B
+ * vanishes in every row at or below the rank.  The particular solution sets
+ * every free variable to zero: X[pivots[t]][j] = reduced B[t][j], other rows 0.
+ * X is nA x k with leading dimension ldx; inconsistent columns of X are 0.
+ */
+int oracle_solve(uint32_t *M, int64_t m, int64_t nA, int64_t k, int64_t ld,
+                 uint32_t p, int nthreads, uint32_t *X, int64_t ldx,
+                 uint8_t *consistent, int32_t *rank, int32_t *pivots) {
+    if (k < 0 || ldx < k) return -1;
+    int rc = oracle_rref(M, m, nA + k, ld, p, nA, -1, nthreads, rank, pivots, NULL);
+    if (rc) return rc;
+    const int64_t r = *rank;
+    for (int64_t i = 0; i < nA; i++)
+        for (int64_t j = 0; j < k; j++) X[i * ldx + j] = 0;
+    for (int64_t j = 0; j < k; j++) {
+        int ok = 1;
+        for (int64_t i = r; i < m; i++)
+            if (M[i * ld + nA + j] != 0) { ok = 0; break; }
+        consistent[j] = (uint8_t)ok;
+        if (!ok) continue;
+        for (int64_t t = 0; t < r; t++)
+            X[(int64_t)pivots[t] * ldx + j] = M[t * ld + nA + j];
+    }
+    return 0;
+}

@@ -1,0 +1,46 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each mutant below is a copy of oracle.c with one planted slip (on the CPU,
+never on a GPU).  The pin suite is run against every mutant in a subprocess
+and must fail.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "lu_style_update_skips_rows_above": ("if (i == r) continue;", "if (i <= r) continue;"),
+    "wrong_sign_in_update": ("uint64_t negf = p - f;", "uint64_t negf = f;"),
+    "wrong_inverse_exponent": ("(uint64_t)p - 2, p)", "(uint64_t)p - 3, p)"),
+    "row_swap_dropped": ("if (q != r) {", "if (0) {"),
+    "pivot_column_not_cleared": ("for (int64_t j = c; j < n; j++)\n            row[j]",
+                                 "for (int64_t j = c + 1; j < n; j++)\n            row[j]"),
+    "consistency_reads_wrong_rows": ("for (int64_t i = r; i < m; i++)\n            if (M[",
+                                     "for (int64_t i = r + 1; i < m; i++)\n            if (M["),
+    "pivot_search_from_row_zero": ("for (int64_t i = r; i < C->m; i++) {",
+                                   "for (int64_t i = 0; i < C->m; i++) {"),
+    "solution_read_from_wrong_column": ("X[(int64_t)pivots[t] * ldx + j] = M[t * ld + nA + j];",
+                                        "X[(int64_t)t * ldx + j] = M[t * ld + nA + j];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_fail_on_mutant(name, tmp_path):
+    before, after = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(before) == 1, f"mutation site for {name} not found exactly once"
+    mut = tmp_path / "oracle_mut.c"
+    mut.write_text(src.replace(before, after))
+    lib = tmp_path / "liboracle_mut.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", str(lib), str(mut)],
+                   check=True)
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
