@@ -1,0 +1,174 @@
+/*
+ * linac.h -- C ABI of the GB300 (sm_103a) exact mod-p row-reduction library.
+ *
+ * The library computes the reduced row-echelon form (RREF), rank, pivot
+ * columns and particular solutions of linear systems over the prime field
+ * Z/pZ for odd primes p < 2^31, with entries stored as uint32_t residues.
+ * It follows the method of "Linac: linear algebra with CUDA over finite
+ * fields": partially pivoted Gauss-Jordan elimination to RREF (section 3.2,
+ * "Gaussian elimination on GPUs"), the RREF kept in the input's shape with
+ * zero rows at the bottom (section 2.3), and solutions read off the reduced
+ * augmented matrix (section 5.2, "Solving linear systems").
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device; the
+ *    caller allocates and owns them.  Matrices are row-major with a leading
+ *    dimension (ld, in elements) that is a multiple of 4 and >= the number of
+ *    columns, and must start 16-byte aligned (section 3.2, "Number types":
+ *    rows are padded so 128-bit accesses never cross a row).
+ *  - Entries must be canonical residues in [0, p).  Larger entries are not
+ *    reduced and give undefined results.
+ *  - p must be an odd prime below 2^31 (checked on the host with a
+ *    deterministic Miller-Rabin test); otherwise LINAC_ERR_PRIME.
+ *  - All calls are asynchronous and ordered on `stream` (0 = legacy default
+ *    stream).  Argument errors are returned immediately; errors found on the
+ *    device (a bounded wait that gave up) are written to the per-call device
+ *    status word when one is given, otherwise reported by linac_last_device_status().
+ *  - Scratch memory: the library keeps one growing scratch buffer per
+ *    (device, stream), allocated with cudaMalloc on first use.  A call made
+ *    while a stream is being captured into a CUDA graph must therefore be
+ *    preceded by an uncaptured call of at least the same size on that stream.
+ *  - Results are bit-exact: the field is exact, no floating point is used.
+ */
+#ifndef LINAC_H
+#define LINAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cudaStream_t;
+
+typedef enum {
+    LINAC_OK = 0,
+    LINAC_ERR_ARG = 1,        /* bad shape, null pointer, bad option */
+    LINAC_ERR_PRIME = 2,      /* p is not an odd prime below 2^31 */
+    LINAC_ERR_ALIGN = 3,      /* ld not a multiple of 4, or pointer not 16-byte aligned */
+    LINAC_ERR_CUDA = 4,       /* a CUDA runtime call failed */
+    LINAC_ERR_NOMEM = 5,      /* scratch allocation failed */
+    LINAC_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    LINAC_ERR_RANGE = 7,      /* an input entry is not in [0, p) (validation pass) */
+    LINAC_ERR_UNSUPPORTED = 8 /* size or option outside what this build supports */
+} linac_status;
+
+/* Trailing-update arithmetic (the rank-k update C <- C - A*B mod p that
+ * dominates the O(n^3) work). */
+typedef enum {
+    LINAC_PATH_AUTO = 0,   /* fastest measured path on this device */
+    LINAC_PATH_PLAIN = 1,  /* CUDA cores: lazy signed 64-bit accumulation */
+    LINAC_PATH_LIMB = 2    /* integer tensor pipe: four u8 limbs per residue */
+} linac_path;
+
+typedef struct {
+    int32_t path;          /* linac_path */
+    int32_t nb;            /* panel width; 0 = automatic (must be a multiple of 16, <= 128) */
+    int32_t validate;      /* nonzero: check every entry is in [0, p) first */
+    int32_t reserved;
+} linac_options;
+
+/*
+ * linac_rref -- in-place reduced row-echelon form (section 3.2; section 2.3
+ * for the output shape).
+ *   d_A       m x n matrix, row-major, leading dimension ld; overwritten by its
+ *             RREF: row t < rank has a 1 in column d_pivots[t], zeros in every
+ *             other pivot column and in every column left of its pivot; rows
+ *             rank..m-1 are zero.
+ *   d_rank    one int32_t: the rank.
+ *   d_pivots  min(m, n) int32_t: pivot columns in increasing order, -1 after
+ *             the rank.
+ * Pivots are searched over all n columns, as the paper's column loop does
+ * (section 3.2, "Looping"), so an inconsistent augmented column becomes a
+ * pivot (section 5.2).
+ * Errors: LINAC_ERR_ARG (m or n < 0, null pointers with m*n > 0, ld < n),
+ * LINAC_ERR_ALIGN, LINAC_ERR_PRIME, LINAC_ERR_NOMEM, LINAC_ERR_CUDA.
+ */
+linac_status linac_rref(uint32_t *d_A, int64_t m, int64_t n, int64_t ld, uint32_t p,
+                        int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
+
+/* linac_rref with options (NULL = defaults).  ncols_search limits the pivot
+ * search to columns [0, ncols_search) while still reducing all n columns
+ * (pass n for plain RREF). */
+linac_status linac_rref_ex(uint32_t *d_A, int64_t m, int64_t n, int64_t ld, uint32_t p,
+                           int64_t ncols_search, int32_t *d_rank, int32_t *d_pivots,
+                           const linac_options *opts, cudaStream_t stream);
+
+/*
+ * linac_solve -- particular solutions of A X = B over Z/pZ (section 5.2).
+ *   d_A  m x nA (ldA), d_B m x k (ldB): read only.
+ *   d_X  nA x k (ldX): X[pivots[t]][j] = reduced B[t][j], free variables 0
+ *        (section 5.2: the particular solution sets the free variables to
+ *        zero); an inconsistent column j of X is all zero.
+ *   d_consistent  k bytes: 1 iff rank(A) == rank(A | b_j) (section 5.2).
+ *   d_rank, d_pivots  rank of A and its pivot columns (min(m, nA) entries,
+ *        -1 after the rank).
+ * The augmented matrix [A | B] is reduced in library scratch memory with the
+ * pivot search restricted to A's columns.  Same errors as linac_rref;
+ * ldX must be >= k (a multiple of 4 is not required for X).
+ */
+linac_status linac_solve(const uint32_t *d_A, int64_t m, int64_t nA, int64_t ldA,
+                         const uint32_t *d_B, int64_t k, int64_t ldB, uint32_t p,
+                         uint32_t *d_X, int64_t ldX, uint8_t *d_consistent,
+                         int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
+
+/* linac_solve with options (NULL = defaults). */
+linac_status linac_solve_ex(const uint32_t *d_A, int64_t m, int64_t nA, int64_t ldA,
+                            const uint32_t *d_B, int64_t k, int64_t ldB, uint32_t p,
+                            uint32_t *d_X, int64_t ldX, uint8_t *d_consistent,
+                            int32_t *d_rank, int32_t *d_pivots,
+                            const linac_options *opts, cudaStream_t stream);
+
+/* Flags for linac_rref_batched. */
+#define LINAC_SHARED_PATTERN 1u  /* all systems share one pivot pattern: find it
+                                    with one probe elimination, reuse it, and fall
+                                    back to a full search for any system where a
+                                    reused pivot vanishes */
+
+/*
+ * linac_rref_batched -- in-place RREF of `batch` independent systems in one
+ * launch sequence (no host synchronisation; capturable in a CUDA graph once
+ * the scratch buffer exists).  The paper motivates many small systems by
+ * evaluating polynomial ansatze at many points (section 3.3); each system is
+ * reduced exactly as linac_rref would.
+ *   d_data        packed matrices; system s is d_m[s] x d_n[s] with leading
+ *                 dimension d_ld[s] (a multiple of 4) starting at element
+ *                 d_offsets[s] (a multiple of 4).
+ *   d_nsearch     per-system pivot-search limit (NULL = all columns).
+ *   d_ranks       batch int32_t ranks.
+ *   d_pivots      pivot columns of system s at d_pivots + d_piv_offsets[s]
+ *                 (min(m, n) entries each, -1 after the rank).
+ *   d_status      batch int32_t per-system status (NULL = not reported):
+ *                 0 ok; with LINAC_SHARED_PATTERN, bit 8 (0x100) marks a
+ *                 system that needed the full pivot search.
+ *   max_m, max_n  upper bounds of d_m and d_n (host values, used to size the
+ *                 launch); systems with n > 1024 or m > 65535 are rejected.
+ * Errors: as linac_rref; LINAC_ERR_UNSUPPORTED for sizes above the limits.
+ */
+linac_status linac_rref_batched(uint32_t *d_data, const int64_t *d_offsets,
+                                const int32_t *d_m, const int32_t *d_n, const int32_t *d_ld,
+                                const int32_t *d_nsearch, int32_t batch,
+                                int32_t max_m, int32_t max_n, uint32_t p, uint32_t flags,
+                                int32_t *d_ranks, int32_t *d_pivots, const int64_t *d_piv_offsets,
+                                int32_t *d_status, cudaStream_t stream);
+
+/* Scratch bytes linac_rref_ex needs for an m x n problem with these options
+ * (the library allocates them itself; exposed for capacity planning). */
+size_t linac_workspace_bytes(int64_t m, int64_t n, const linac_options *opts);
+
+/* Status word written by device-side checks of the most recent call on this
+ * host thread (LINAC_OK when none fired); synchronises `stream`. */
+linac_status linac_last_device_status(cudaStream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char *linac_status_string(linac_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t linac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LINAC_H */

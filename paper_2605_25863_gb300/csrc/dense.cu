@@ -1,0 +1,549 @@
+// dense.cu -- blocked right-looking Gauss-Jordan elimination of one dense
+// matrix over Z/pZ on sm_103a, with every piece of state kept on the device.
+//
+// The paper (section 3.2) reduces one column per iteration: pivot search,
+// row swap, rescale of the pivot row by the inverse of its head, and a
+// rank-1 update of every other row.  Here the same elimination is blocked by
+// panels of nb columns [c0, c1):
+//
+//   1. panel_kernel   (cooperative)  finds the k <= nb pivots of the panel
+//      among the rows not yet used (the current rank r .. m-1).  One grid
+//      barrier per column; the elimination inside the panel is fraction-free
+//      (row_i <- h * row_i - f_i * pivot_row), so no inverse is on this
+//      sequential path.  It records the pivot rows Pi, pivot columns J and,
+//      in place of the eliminated entries, the multipliers f.
+//   2. gather_*       F = M[:, J] (the multipliers of the final update, in
+//      balanced signed form, stored transposed) and W = M[Pi, c0:n].
+//   3. heads_inverse  batched inverses of the k pivot heads (binary extended
+//      Euclid, one thread each).
+//   4. trsm_kernel    replays the panel's fraction-free recurrence on W,
+//      scales each row by its head's inverse and back-substitutes, giving
+//      the k reduced pivot rows R (identity at J).
+//   5. move_kernel    rows of [r, r+k) that are not pivots move to the pivot
+//      rows' old places (the paper's row swap, done once per panel).
+//   6. update_plain   every row d outside [r, r+k):  M[d, c0:n] -= F[d] * R
+//      (mod p), the O(n^3) trailing update; rows r..r+k-1 receive R.
+//   7. finish_kernel  appends J to the pivot list and advances r by k.
+//
+// Because R is fully reduced (identity at the pivot columns), the update
+// multipliers are simply each row's entries at the pivot columns, and the
+// update clears those columns in every other row, above and below: that is
+// Gauss-Jordan (reduced echelon form), not LU.
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+
+#include "linac_host.h"
+#include "update.cuh"
+
+namespace linac {
+
+constexpr int PANEL_THREADS = 256;
+constexpr int TRSM_TB = 64;
+
+// ---------------------------------------------------------------------------
+// Initialisation and bookkeeping
+
+__global__ void init_kernel(DenseState* st, int32_t* d_pivots, int64_t npiv, int32_t* d_rank) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npiv;
+         i += (int64_t)gridDim.x * blockDim.x)
+        d_pivots[i] = -1;
+    if (blockIdx.x == 0) {
+        for (int t = threadIdx.x; t < NB_MAX; t += blockDim.x) st->best[t] = INT_MAX;
+        if (threadIdx.x == 0) {
+            st->r = 0;
+            st->k = 0;
+            st->bar.count = 0;
+            st->bar.gen = 0;
+            *d_rank = 0;
+        }
+    }
+}
+
+__global__ void finish_kernel(DenseState* st, int32_t* d_pivots, int32_t* d_rank) {
+    const int k = st->k, r = st->r;
+    __syncthreads();
+    for (int t = threadIdx.x; t < k; t += blockDim.x) d_pivots[r + t] = st->J[t];
+    for (int t = threadIdx.x; t < NB_MAX; t += blockDim.x) st->best[t] = INT_MAX;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->r = r + k;
+        st->k = 0;
+        *d_rank = r + k;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 1. Panel factorisation (cooperative launch, one row slab per block)
+//
+// Shared memory: S_max x (w+1) residues (the slab, padded against bank
+// conflicts), the broadcast pivot row, the owned-pivot list and pivot flags.
+
+__global__ void __launch_bounds__(PANEL_THREADS)
+panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, int S_max,
+             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int SW = w + 1;
+    uint32_t* P = sm;
+    uint32_t* prow = P + (size_t)S_max * SW;
+    int* own = (int*)(prow + NB_MAX);
+    unsigned char* isp = (unsigned char*)(own + NB_MAX);
+    __shared__ int s_red[PANEL_THREADS / 32];
+    __shared__ int s_min;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int G = gridDim.x, b = blockIdx.x;
+    const int64_t r = st->r;
+    const int64_t left = m - r;
+    const int S = left > 0 ? (int)((left + G - 1) / G) : 0;
+    const int64_t lo = r + (int64_t)b * S;
+    int nrows = 0;
+    if (S > 0 && lo < m) nrows = (int)min((int64_t)S, m - lo);
+
+    for (int64_t e = tid; e < (int64_t)nrows * w; e += blockDim.x) {
+        const int i = (int)(e / w), j = (int)(e % w);
+        P[i * SW + j] = M[(lo + i) * ld + c0 + j];
+    }
+    for (int i = tid; i < nrows; i += blockDim.x) isp[i] = 0;
+    for (int t = tid; t < NB_MAX; t += blockDim.x) own[t] = -1;
+    __syncthreads();
+
+    int kk = 0;
+    for (int cc = 0; cc < w; ++cc) {
+        // lowest local non-pivot row with a nonzero entry in column cc
+        int ci = INT_MAX;
+        for (int i = tid; i < nrows; i += blockDim.x)
+            if (!isp[i] && P[i * SW + cc] != 0) { ci = i; break; }
+        for (int o = 16; o; o >>= 1) ci = min(ci, __shfl_xor_sync(0xffffffffu, ci, o));
+        if (lane == 0) s_red[warp] = ci;
+        __syncthreads();
+        if (warp == 0) {
+            int v = lane < nwarps ? s_red[lane] : INT_MAX;
+            for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) s_min = v;
+        }
+        __syncthreads();
+        const int imin = s_min;
+        const int par = cc & 1;
+        if (imin != INT_MAX) {
+            // publish this block's candidate row before arriving at the barrier;
+            // buffers alternate by column parity so a candidate is never
+            // overwritten while another block may still read it
+            uint32_t* dst = cand + ((size_t)par * G + b) * NB_MAX;
+            for (int j = tid; j < w; j += blockDim.x) dst[j] = P[imin * SW + j];
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicMin(&st->best[cc], (int)(lo + imin));
+        }
+        if (!grid_sync(&st->bar, (unsigned)G, status)) return;
+        const int q = __ldcg(&st->best[cc]);
+        if (q == INT_MAX) continue;   // no pivot in this column (uniform branch)
+        const int owner = (int)((q - r) / S);
+        const uint32_t* src = cand + ((size_t)par * G + owner) * NB_MAX;
+        for (int j = tid; j < w; j += blockDim.x) prow[j] = __ldcg(src + j);
+        if (tid == 0) {
+            if (b == owner) { isp[q - lo] = 1; own[kk] = (int)(q - lo); }
+            if (b == 0) { st->Pi[kk] = q; st->J[kk] = c0 + cc; }
+        }
+        __syncthreads();
+        const uint32_t h = prow[cc];
+        // fraction-free elimination of column cc from the other non-pivot
+        // rows; the multiplier f stays stored in column cc
+        for (int i = warp; i < nrows; i += nwarps) {
+            if (isp[i]) continue;
+            uint32_t* row = P + i * SW;
+            const uint32_t fi = row[cc];
+            if (fi == 0) continue;
+            const uint32_t nf = f.p - fi;
+            for (int j = cc + 1 + lane; j < w; j += 32) row[j] = mul2add(h, row[j], nf, prow[j], f);
+        }
+        ++kk;
+        __syncthreads();
+    }
+    for (int t = 0; t < kk; ++t) {
+        const int i = own[t];
+        if (i < 0) continue;
+        for (int j = tid; j < w; j += blockDim.x) panelU[(size_t)t * NB_MAX + j] = P[i * SW + j];
+    }
+    if (b == 0 && tid == 0) st->k = kk;
+}
+
+// ---------------------------------------------------------------------------
+// 2. Gathers
+
+// Ft[t][i] = balanced(M[i][J_t]) for every row i, zero for t in [k, kpad).
+// A block stages 64 rows' panel segments in shared memory, then writes the
+// transposed multipliers with coalesced stores.
+__global__ void __launch_bounds__(256)
+gather_f_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f,
+                const DenseState* __restrict__ st, int32_t* __restrict__ Ft, int64_t ldF) {
+    __shared__ uint32_t seg[64][NB_MAX + 1];
+    __shared__ int Jl[NB_MAX];
+    const int k = st->k;
+    if (k == 0) return;
+    const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
+    const int64_t row0 = (int64_t)blockIdx.x * 64;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) Jl[t] = st->J[t] - c0;
+    for (int e = threadIdx.x; e < 64 * w; e += blockDim.x) {
+        const int i = e / w, j = e % w;
+        const int64_t row = row0 + i;
+        seg[i][j] = row < m ? M[row * ld + c0 + j] : 0u;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kpad * 64; e += blockDim.x) {
+        const int t = e >> 6, i = e & 63;
+        const int64_t row = row0 + i;
+        if (row < m) Ft[(int64_t)t * ldF + row] = t < k ? to_balanced(seg[i][Jl[t]], f) : 0;
+    }
+}
+
+// W[t][j] = M[Pi_t][c0 + j], j < n - c0.
+__global__ void gather_w_kernel(const uint32_t* __restrict__ M, int64_t ld, int64_t ncols, int c0,
+                                const DenseState* __restrict__ st, uint32_t* __restrict__ W,
+                                int64_t ldW) {
+    const int t = blockIdx.y;
+    if (t >= st->k) return;
+    const uint32_t* src = M + (int64_t)st->Pi[t] * ld + c0;
+    uint32_t* dst = W + (int64_t)t * ldW;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ncols;
+         j += (int64_t)gridDim.x * blockDim.x)
+        dst[j] = src[j];
+}
+
+// ---------------------------------------------------------------------------
+// 3. Batched inverses of the pivot heads h_t = panelU[t][J_t - c0].
+
+__global__ void heads_inverse_kernel(DenseState* st, const uint32_t* __restrict__ panelU, int c0,
+                                     uint32_t p, int* status) {
+    const int k = st->k;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        const uint32_t h = panelU[(size_t)t * NB_MAX + (st->J[t] - c0)];
+        if (h == 0) atomicCAS(status, 0, (int)LINAC_ERR_RANGE);   // cannot happen for p prime
+        st->hinv[t] = inverse_mod(h, p);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4. TRSM-style reduction of the pivot rows, one column tile per block.
+//
+// V = W[:, tile].  Forward: for s = 0..k-2 and every t > s with multiplier
+// f_ts = panelU[t][J_s] != 0: V_t <- h_s V_t - f_ts V_s (the panel's own
+// recurrence, now on full rows).  Scale: V_t <- V_t / h_t.  Backward: for
+// s = k-1..1 and t < s: V_t <- V_t - c_ts V_s with c_ts = panelU[t][J_s] / h_t,
+// which is V_t's entry at J_s after the forward pass and the scaling.
+__global__ void __launch_bounds__(256)
+trsm_kernel(const uint32_t* __restrict__ W, int64_t ldW, int64_t ncols, int c0, Field f,
+            const DenseState* __restrict__ st, const uint32_t* __restrict__ panelU,
+            int32_t* __restrict__ R, int64_t ldR) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ uint32_t hs[NB_MAX], hinv[NB_MAX];
+    __shared__ int Jl[NB_MAX];
+    const int k = st->k;
+    if (k == 0) return;
+    const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
+    constexpr int TB = TRSM_TB;
+    uint32_t* V = sm;                         // NB_MAX x TB
+    uint32_t* Co = V + NB_MAX * TB;           // k x k coefficients, row stride NB_MAX
+    const int64_t j0 = (int64_t)blockIdx.x * TB;
+    const int tid = threadIdx.x;
+    for (int t = tid; t < k; t += blockDim.x) {
+        Jl[t] = st->J[t] - c0;
+        hinv[t] = st->hinv[t];
+    }
+    __syncthreads();
+    for (int t = tid; t < k; t += blockDim.x) hs[t] = panelU[(size_t)t * NB_MAX + Jl[t]];
+    for (int e = tid; e < k * k; e += blockDim.x) {
+        const int t = e / k, s = e % k;
+        const uint32_t v = panelU[(size_t)t * NB_MAX + Jl[s]];
+        Co[t * NB_MAX + s] = s > t ? mulmod(v, hinv[t], f) : v;
+    }
+    for (int e = tid; e < k * TB; e += blockDim.x) {
+        const int t = e / TB, j = e % TB;
+        V[t * TB + j] = (j0 + j < ncols) ? W[(int64_t)t * ldW + j0 + j] : 0u;
+    }
+    __syncthreads();
+    for (int s = 0; s + 1 < k; ++s) {
+        const uint32_t h = hs[s];
+        for (int e = tid; e < (k - 1 - s) * TB; e += blockDim.x) {
+            const int t = s + 1 + e / TB, j = e % TB;
+            const uint32_t fts = Co[t * NB_MAX + s];
+            if (fts) V[t * TB + j] = mul2add(h, V[t * TB + j], f.p - fts, V[s * TB + j], f);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < k * TB; e += blockDim.x) V[e] = mulmod(V[e], hinv[e / TB], f);
+    __syncthreads();
+    for (int s = k - 1; s >= 1; --s) {
+        for (int e = tid; e < s * TB; e += blockDim.x) {
+            const int t = e / TB, j = e % TB;
+            const uint32_t c = Co[t * NB_MAX + s];
+            if (c) V[t * TB + j] = mul2add(1u, V[t * TB + j], f.p - c, V[s * TB + j], f);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < kpad * TB; e += blockDim.x) {
+        const int t = e / TB, j = e % TB;
+        if (j0 + j < ncols) R[(int64_t)t * ldR + j0 + j] = t < k ? to_balanced(V[t * TB + j], f) : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 5. Row moves: positions of [r, r+k) that do not hold a pivot row send their
+// row (and multipliers) to the pivot rows' old positions outside [r, r+k).
+// Block a handles pair a; every block derives the same pairing.
+
+__global__ void __launch_bounds__(256)
+move_kernel(uint32_t* __restrict__ M, int64_t ld, int64_t n, int c0, const DenseState* __restrict__ st,
+            int32_t* __restrict__ Ft, int64_t ldF) {
+    __shared__ int srcs[NB_MAX], dsts[NB_MAX];
+    __shared__ unsigned char occ[NB_MAX];
+    __shared__ int npairs;
+    const int k = st->k;
+    if (k == 0) return;
+    const int r = st->r;
+    if (threadIdx.x == 0) {
+        for (int d = 0; d < k; ++d) occ[d] = 0;
+        for (int t = 0; t < k; ++t) {
+            const int q = st->Pi[t];
+            if (q >= r && q < r + k) occ[q - r] = 1;
+        }
+        int a = 0;
+        for (int d = 0; d < k; ++d)
+            if (!occ[d]) srcs[a++] = r + d;
+        int bcount = 0;
+        for (int t = 0; t < k; ++t) {
+            const int q = st->Pi[t];
+            if (q < r || q >= r + k) dsts[bcount++] = q;
+        }
+        npairs = a;   // equals bcount: |D \ S| = |S \ D|
+    }
+    __syncthreads();
+    const int a = blockIdx.x;
+    if (a >= npairs) return;
+    const int64_t src = srcs[a], dst = dsts[a];
+    for (int64_t j = c0 + threadIdx.x; j < n; j += blockDim.x) M[dst * ld + j] = M[src * ld + j];
+    const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
+    for (int t = threadIdx.x; t < kpad; t += blockDim.x)
+        Ft[(int64_t)t * ldF + dst] = Ft[(int64_t)t * ldF + src];
+}
+
+// ---------------------------------------------------------------------------
+// Solve helpers and validation
+
+__global__ void pack_kernel(const uint32_t* __restrict__ A, int64_t m, int64_t nA, int64_t ldA,
+                            const uint32_t* __restrict__ B, int64_t k, int64_t ldB,
+                            uint32_t* __restrict__ Mx, int64_t ldM) {
+    const int64_t ncols = nA + k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * ldM;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ldM, j = e % ldM;
+        uint32_t v = 0;
+        if (j < nA) v = A[i * ldA + j];
+        else if (j < ncols) v = B[i * ldB + (j - nA)];
+        Mx[e] = v;
+    }
+}
+
+// One block per right-hand side j: consistent iff the reduced column vanishes
+// at and below the rank (section 5.2); X column from the pivot rows, free
+// variables zero.
+__global__ void __launch_bounds__(256)
+extract_kernel(const uint32_t* __restrict__ Mx, int64_t m, int64_t nA, int64_t ldM,
+               const int32_t* __restrict__ d_rank, const int32_t* __restrict__ d_pivots,
+               uint32_t* __restrict__ X, int64_t ldX, uint8_t* __restrict__ cons) {
+    __shared__ int s_bad;
+    const int64_t j = blockIdx.x;
+    const int rank = *d_rank;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    int bad = 0;
+    for (int64_t i = rank + threadIdx.x; i < m; i += blockDim.x)
+        if (Mx[i * ldM + nA + j] != 0) bad = 1;
+    if (bad) atomicOr(&s_bad, 1);
+    __syncthreads();
+    const int ok = !s_bad;
+    if (threadIdx.x == 0) cons[j] = (uint8_t)ok;
+    for (int64_t i = threadIdx.x; i < nA; i += blockDim.x) X[i * ldX + j] = 0;
+    __syncthreads();
+    if (!ok) return;
+    for (int t = threadIdx.x; t < rank; t += blockDim.x)
+        X[(int64_t)d_pivots[t] * ldX + j] = Mx[(int64_t)t * ldM + nA + j];
+}
+
+__global__ void validate_kernel(const uint32_t* __restrict__ A, int64_t m, int64_t n, int64_t ld,
+                                uint32_t p, int* status) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / n, j = e % n;
+        if (A[i * ld + j] >= p) { atomicCAS(status, 0, (int)LINAC_ERR_RANGE); return; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host driver
+
+namespace {
+
+struct DenseLayout {
+    size_t off_state, off_cand, off_panel, off_ft, off_w, off_r, total;
+    int64_t ldF, ldW;
+};
+
+DenseLayout dense_layout(int64_t m, int64_t n, int G) {
+    DenseLayout L;
+    size_t o = 0;
+    L.off_state = o; o = align_up(o + sizeof(DenseState), 256);
+    L.off_cand = o;  o = align_up(o + (size_t)2 * G * NB_MAX * 4, 256);
+    L.off_panel = o; o = align_up(o + (size_t)NB_MAX * NB_MAX * 4, 256);
+    L.ldF = (int64_t)align_up((size_t)std::max<int64_t>(m, 1), 4);
+    L.off_ft = o;    o = align_up(o + (size_t)NB_MAX * L.ldF * 4, 256);
+    L.ldW = (int64_t)align_up((size_t)std::max<int64_t>(n, 1), 4);
+    L.off_w = o;     o = align_up(o + (size_t)NB_MAX * L.ldW * 4, 256);
+    L.off_r = o;     o = align_up(o + (size_t)NB_MAX * L.ldW * 4, 256);
+    L.total = o;
+    return L;
+}
+
+int panel_grid(int64_t m) {
+    const int nsm = sm_count();
+    int64_t g = (m + 127) / 128;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, nsm));
+}
+
+size_t panel_smem(int S_max, int w) {
+    return (size_t)S_max * (w + 1) * 4 + NB_MAX * 4 + NB_MAX * 4 + (size_t)S_max + 16;
+}
+
+}  // namespace
+
+int dense_default_nb(int64_t m, int64_t n) {
+    (void)n;
+    return m >= 2048 ? 128 : 64;
+}
+
+size_t dense_workspace_bytes(int64_t m, int64_t n, int nb) {
+    (void)nb;
+    return dense_layout(m, n, panel_grid(m)).total;
+}
+
+linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Field& f,
+                        int64_t nsearch, int32_t* d_rank, int32_t* d_pivots, int path, int nb,
+                        cudaStream_t stream) {
+    int* status = status_word(stream);
+    if (!status) return LINAC_ERR_NOMEM;
+    const int64_t npiv = std::min(m, nsearch);
+    if (nb <= 0) nb = dense_default_nb(m, n);
+    if (nb % UPD_BK != 0 || nb > NB_MAX) return LINAC_ERR_ARG;
+
+    const int G = panel_grid(m);
+    const int S_max = (int)((m + G - 1) / G);
+    size_t psmem = panel_smem(S_max, nb);
+    int max_smem = 0;
+    LINAC_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
+    while (psmem > (size_t)max_smem - 1024 && nb > UPD_BK) {   // very tall matrices: narrower panels
+        nb -= UPD_BK;
+        psmem = panel_smem(S_max, nb);
+    }
+    if (psmem > (size_t)max_smem - 1024) return LINAC_ERR_UNSUPPORTED;
+    if ((m + UPD_BM - 1) / UPD_BM > 65535) return LINAC_ERR_UNSUPPORTED;
+
+    DenseLayout L = dense_layout(m, n, G);
+    void* base = nullptr;
+    linac_status st_ = scratch_get(stream, L.total, &base);
+    if (st_ != LINAC_OK) return st_;
+    char* ws = (char*)base;
+    DenseState* st = (DenseState*)(ws + L.off_state);
+    uint32_t* cand = (uint32_t*)(ws + L.off_cand);
+    uint32_t* panelU = (uint32_t*)(ws + L.off_panel);
+    int32_t* Ft = (int32_t*)(ws + L.off_ft);
+    uint32_t* W = (uint32_t*)(ws + L.off_w);
+    int32_t* R = (int32_t*)(ws + L.off_r);
+
+    LINAC_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)psmem));
+    const size_t tsmem = (size_t)(NB_MAX * TRSM_TB + NB_MAX * NB_MAX) * 4;
+    LINAC_CUDA_TRY(cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tsmem));
+    int occ = 0;
+    LINAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_kernel, PANEL_THREADS, psmem));
+    if (occ < 1 || G > occ * sm_count()) return LINAC_ERR_UNSUPPORTED;
+
+    LimbScratch limb{};
+    bool limb_ok = false;
+    if (path == LINAC_PATH_LIMB) {
+        limb.m_pad = (int64_t)align_up((size_t)std::max<int64_t>(m, 1), UPD_BM);
+        limb.n_pad = (int64_t)align_up((size_t)std::max<int64_t>(n, 1), UPD_BN);
+        const size_t fbytes = (size_t)4 * limb.m_pad * NB_MAX, rbytes = (size_t)4 * limb.n_pad * NB_MAX;
+        void* lb = nullptr;
+        st_ = scratch_get_slot(stream, 3, fbytes + rbytes, &lb);
+        if (st_ != LINAC_OK) return st_;
+        limb.Fl = (uint8_t*)lb;
+        limb.Rl = (uint8_t*)lb + fbytes;
+        limb_ok = true;
+    }
+    {
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((npiv + 255) / 256, 1024));
+        init_kernel<<<(unsigned)blocks, 256, 0, stream>>>(st, d_pivots, npiv, d_rank);
+        LINAC_CUDA_TRY(cudaGetLastError());
+    }
+    if (m == 0 || n == 0) return LINAC_OK;
+
+    for (int64_t c0 = 0; c0 < nsearch; c0 += nb) {
+        const int w = (int)std::min<int64_t>(nb, nsearch - c0);
+        const int64_t ncols = n - c0;
+        {
+            const uint32_t* Mc = dA;
+            int64_t m_ = m, ld_ = ld;
+            int c0_ = (int)c0, w_ = w, S_ = S_max;
+            Field f_ = f;
+            void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status};
+            LINAC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_kernel, dim3(G), dim3(PANEL_THREADS),
+                                                       args, psmem, stream));
+        }
+        gather_f_kernel<<<(unsigned)((m + 63) / 64), 256, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, Ft, L.ldF);
+        {
+            const unsigned gx = (unsigned)std::min<int64_t>((ncols + 1023) / 1024, 64);
+            gather_w_kernel<<<dim3(std::max(1u, gx), NB_MAX), 256, 0, stream>>>(dA, ld, ncols, (int)c0, st, W, L.ldW);
+        }
+        heads_inverse_kernel<<<1, NB_MAX, 0, stream>>>(st, panelU, (int)c0, f.p, status);
+        trsm_kernel<<<(unsigned)((ncols + TRSM_TB - 1) / TRSM_TB), 256, tsmem, stream>>>(
+            W, L.ldW, ncols, (int)c0, f, st, panelU, R, L.ldW);
+        move_kernel<<<NB_MAX, 256, 0, stream>>>(dA, ld, n, (int)c0, st, Ft, L.ldF);
+        linac_status us = launch_update(path, dA, m, n, ld, (int)c0, f, st, Ft, L.ldF, R, L.ldW,
+                                       limb_ok ? &limb : nullptr, stream);
+        if (us != LINAC_OK) return us;
+        finish_kernel<<<1, NB_MAX, 0, stream>>>(st, d_pivots, d_rank);
+        LINAC_CUDA_TRY(cudaGetLastError());
+    }
+    return LINAC_OK;
+}
+
+linac_status solve_pack(const uint32_t* dA, int64_t m, int64_t nA, int64_t ldA, const uint32_t* dB,
+                        int64_t k, int64_t ldB, uint32_t* dM, int64_t ldM, cudaStream_t stream) {
+    if (m == 0) return LINAC_OK;
+    const int64_t total = m * ldM;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096));
+    pack_kernel<<<blocks, 256, 0, stream>>>(dA, m, nA, ldA, dB, k, ldB, dM, ldM);
+    LINAC_CUDA_TRY(cudaGetLastError());
+    return LINAC_OK;
+}
+
+linac_status solve_extract(const uint32_t* dM, int64_t m, int64_t nA, int64_t k, int64_t ldM,
+                           const int32_t* d_rank, const int32_t* d_pivots, uint32_t* dX, int64_t ldX,
+                           uint8_t* d_consistent, cudaStream_t stream) {
+    if (k == 0) return LINAC_OK;
+    extract_kernel<<<(unsigned)k, 256, 0, stream>>>(dM, m, nA, ldM, d_rank, d_pivots, dX, ldX, d_consistent);
+    LINAC_CUDA_TRY(cudaGetLastError());
+    return LINAC_OK;
+}
+
+linac_status validate_range(const uint32_t* dA, int64_t m, int64_t n, int64_t ld, uint32_t p,
+                            int* d_status, cudaStream_t stream) {
+    if (m == 0 || n == 0) return LINAC_OK;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((m * n + 255) / 256, 4096));
+    validate_kernel<<<blocks, 256, 0, stream>>>(dA, m, n, ld, p, d_status);
+    LINAC_CUDA_TRY(cudaGetLastError());
+    return LINAC_OK;
+}
+
+}  // namespace linac

@@ -1,0 +1,156 @@
+// linac_device.cuh -- device-side building blocks shared by the sm_103a kernels:
+// modular arithmetic for odd primes p < 2^31, the pivot inverse, a bounded
+// grid barrier for cooperative launches, and the on-device state records.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/linac.h"
+
+namespace linac {
+
+// ---------------------------------------------------------------------------
+// Per-prime constants, computed once per call on the host.
+//
+//  mu   = floor(2^64 / p)            Barrett constant for 64-bit operands.
+//  c32  = 2^32 mod p                 folds a signed 64-bit lazy accumulator
+//                                    H*2^32 + L into H*c32 + L.
+//  half = (p - 1) / 2                residues r > half are stored as r - p
+//                                    ("balanced" signed form, |x| <= half).
+//  fold = number of balanced products |x*y| <= half^2 that may be added to a
+//         folded accumulator without leaving the signed 64-bit range.
+struct Field {
+    uint32_t p;
+    uint32_t c32;
+    uint64_t mu;
+    uint32_t half;
+    uint32_t fold;
+};
+
+__host__ __device__ inline uint32_t lo32(uint64_t x) { return (uint32_t)x; }
+
+// x mod p for any 64-bit x.  Barrett: q = floor(x * mu / 2^64) satisfies
+// x/p - 2 < q <= x/p, so x - q*p lies in [0, 2p) and one conditional
+// subtraction finishes (p < 2^31 keeps every intermediate in 64 bits).
+__device__ __forceinline__ uint32_t reduce64(uint64_t x, const Field& f) {
+    uint64_t q = __umul64hi(x, f.mu);
+    uint64_t r = x - q * (uint64_t)f.p;
+    if (r >= f.p) r -= f.p;
+    return (uint32_t)r;
+}
+
+__device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b, const Field& f) {
+    return reduce64((uint64_t)a * b, f);
+}
+
+// (a*x + b*y) mod p with a, b, x, y in [0, p): the sum of two products is
+// below 2^63, so a single reduction suffices.
+__device__ __forceinline__ uint32_t mul2add(uint32_t a, uint32_t x, uint32_t b, uint32_t y,
+                                            const Field& f) {
+    return reduce64((uint64_t)a * x + (uint64_t)b * y, f);
+}
+
+__device__ __forceinline__ uint32_t addmod(uint32_t a, uint32_t b, const Field& f) {
+    uint32_t s = a + b;                     // < 2^32 since a, b < 2^31
+    return s >= f.p ? s - f.p : s;
+}
+
+__device__ __forceinline__ uint32_t submod(uint32_t a, uint32_t b, const Field& f) {
+    return a >= b ? a - b : a + f.p - b;
+}
+
+// Balanced signed representative of a residue, |result| <= (p-1)/2.
+__device__ __forceinline__ int32_t to_balanced(uint32_t r, const Field& f) {
+    return r > f.half ? (int32_t)(r - f.p) : (int32_t)r;
+}
+
+__device__ __forceinline__ uint32_t from_balanced(int32_t v, const Field& f) {
+    return v < 0 ? (uint32_t)(v + (int32_t)f.p) : (uint32_t)v;
+}
+
+// Signed 64-bit lazy accumulator fold: acc = H*2^32 + L  ->  H*c32 + L, which
+// is congruent mod p and has magnitude below 2^31*c32 + 2^32 <= 2^62 + 2^32.
+__device__ __forceinline__ int64_t fold64(int64_t acc, const Field& f) {
+    int32_t H = (int32_t)(acc >> 32);
+    uint32_t L = (uint32_t)acc;
+    return (int64_t)H * (int64_t)f.c32 + (int64_t)L;
+}
+
+// Canonical residue of a signed 64-bit accumulator with |acc| < 2^63.
+__device__ __forceinline__ uint32_t reduce_signed(int64_t acc, const Field& f) {
+    int64_t t = fold64(acc, f);            // |t| < 2^31 * c32 + 2^32 <= 2^31 * p + 2^32
+    // p * 2^32 is a multiple of p above |t| (2^31 p + 2^32 <= 2^32 p for p >= 2)
+    // and t + p * 2^32 < 2^63, so the sum is a non-negative 64-bit value.
+    uint64_t off = (uint64_t)f.p << 32;
+    return reduce64((uint64_t)(t + (int64_t)off), f);
+}
+
+// Modular inverse of a (0 < a < p, p odd) by the binary extended Euclidean
+// algorithm (Stein's binary gcd, Knuth TAOCP vol. 2 sec. 4.5.2, carrying
+// Bezout coefficients): invariants x1*a = u and x2*a = v (mod p); halving a
+// coefficient first adds p when it is odd, which is exact because p is odd.
+// Returns 0 for a == 0 (no inverse).
+__device__ __forceinline__ uint32_t inverse_mod(uint32_t a, uint32_t p) {
+    if (a == 0) return 0;
+    uint32_t u = a, v = p, x1 = 1, x2 = 0;
+    // each pass removes at least one bit from u or v: <= 62 passes for p < 2^31
+    for (int guard = 0; guard < 256 && u != 1 && v != 1; ++guard) {
+        while ((u & 1u) == 0) {
+            u >>= 1;
+            x1 = (x1 & 1u) ? (uint32_t)(((uint64_t)x1 + p) >> 1) : (x1 >> 1);
+        }
+        while ((v & 1u) == 0) {
+            v >>= 1;
+            x2 = (x2 & 1u) ? (uint32_t)(((uint64_t)x2 + p) >> 1) : (x2 >> 1);
+        }
+        if (u >= v) { u -= v; x1 = x1 >= x2 ? x1 - x2 : x1 + p - x2; }
+        else        { v -= u; x2 = x2 >= x1 ? x2 - x1 : x2 + p - x1; }
+    }
+    return u == 1 ? x1 : x2;
+}
+
+// ---------------------------------------------------------------------------
+// Bounded spin limits.  Every wait on another block gives up after about
+// kSpinCycles clocks, records LINAC_ERR_TIMEOUT in the status word and lets
+// the kernel return, so a fault elsewhere can never hang the device.
+constexpr long long kSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+// Sense-counting grid barrier for kernels launched cooperatively (all blocks
+// co-resident).  Returns false if it gave up (timeout or a status already set).
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, int* status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &bar->gen;
+        unsigned int my_gen = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&bar->count, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long long t0 = clock64();
+            while (*vgen == my_gen) {
+                if (*(volatile int*)status != 0) { ok = 0; break; }
+                if (clock64() - t0 > kSpinCycles) {
+                    atomicCAS(status, 0, (int)LINAC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace linac

@@ -1,0 +1,76 @@
+// linac_host.h -- host-side helpers shared by the library's translation units:
+// per-prime constants, scratch memory, launch error checks.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/linac.h"
+#include "linac_device.cuh"
+
+namespace linac {
+
+// Constants for the prime p (see Field in linac_device.cuh).
+Field make_field(uint32_t p);
+
+// Deterministic Miller-Rabin for 32-bit n with bases 2, 7, 61 (these three
+// bases have no common strong pseudoprime below 4,759,123,141; Jaeschke 1993).
+bool is_prime_u32(uint32_t n);
+
+// Odd prime below 2^31?
+inline bool prime_ok(uint32_t p) { return p >= 3 && p < (1u << 31) && is_prime_u32(p); }
+
+// Scratch memory: one growing device buffer per (device, stream).  The
+// returned pointer stays valid until the next call that grows it on the same
+// (device, stream); growing synchronises the stream first.
+linac_status scratch_get(cudaStream_t stream, size_t bytes, void** ptr);
+// Same, for an independent buffer `slot` (0 = dense elimination, 1 = solve's
+// augmented matrix, 2 = batched driver, 3 = limb planes).
+linac_status scratch_get_slot(cudaStream_t stream, int slot, size_t bytes, void** ptr);
+
+// Device status word of the most recent call on this (device, stream): lives
+// in a small per-(device, stream) allocation that is never freed.
+int* status_word(cudaStream_t stream);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+#define LINAC_CUDA_TRY(expr)                                   \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) {                               \
+            (void)cudaGetLastError();                          \
+            return e_ == cudaErrorMemoryAllocation ? LINAC_ERR_NOMEM : LINAC_ERR_CUDA; \
+        }                                                      \
+    } while (0)
+
+// Number of SMs on the current device (cached).
+int sm_count();
+
+// Dense elimination driver (dense.cu): in-place RREF of the m x n matrix with
+// pivots searched in [0, nsearch).  Scratch comes from scratch_get.
+linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Field& f,
+                        int64_t nsearch, int32_t* d_rank, int32_t* d_pivots,
+                        int path, int nb, cudaStream_t stream);
+size_t dense_workspace_bytes(int64_t m, int64_t n, int nb);
+int dense_default_nb(int64_t m, int64_t n);
+
+// Solve helpers (dense.cu).
+linac_status solve_pack(const uint32_t* dA, int64_t m, int64_t nA, int64_t ldA,
+                        const uint32_t* dB, int64_t k, int64_t ldB,
+                        uint32_t* dM, int64_t ldM, cudaStream_t stream);
+linac_status solve_extract(const uint32_t* dM, int64_t m, int64_t nA, int64_t k, int64_t ldM,
+                           const int32_t* d_rank, const int32_t* d_pivots,
+                           uint32_t* dX, int64_t ldX, uint8_t* d_consistent, cudaStream_t stream);
+
+// Range validation (dense.cu): sets *status = LINAC_ERR_RANGE if any entry >= p.
+linac_status validate_range(const uint32_t* dA, int64_t m, int64_t n, int64_t ld, uint32_t p,
+                            int* d_status, cudaStream_t stream);
+
+// Batched driver (batched.cu).
+linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int32_t* d_m,
+                          const int32_t* d_n, const int32_t* d_ld, const int32_t* d_nsearch,
+                          int32_t batch, int32_t max_m, int32_t max_n, const Field& f,
+                          uint32_t flags, int32_t* d_ranks, int32_t* d_pivots,
+                          const int64_t* d_piv_offsets, int32_t* d_status, cudaStream_t stream);
+
+}  // namespace linac

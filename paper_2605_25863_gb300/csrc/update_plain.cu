@@ -1,0 +1,157 @@
+// update_plain.cu -- trailing update on the CUDA cores (the paper's "Row
+// reduce" of section 3.2, blocked to rank k): C <- C - F R mod p.
+//
+// Arithmetic: F and R hold balanced residues |x| <= (p-1)/2, so every product
+// satisfies |x y| <= ((p-1)/2)^2 < 2^60.  Each output accumulates its products
+// exactly in a signed 64-bit register (one IMAD.WIDE per field multiply-add);
+// after every FOLD products the accumulator H*2^32 + L is folded to
+// H*(2^32 mod p) + L, which keeps |acc| < 2^62 + 2^32 so that FOLD more
+// products stay below 2^63 (the host derives FOLD >= 4 from p; FOLD = 8 for
+// the pseudo-Mersenne primes 2^31 - 1 and 2^31 - 19).  One Barrett reduction
+// per output and panel finishes the job.  No floating point anywhere.
+//
+// Tiling: 128 x 128 output tile per 256-thread block, 8 x 8 outputs per
+// thread (two 4-row and two 4-column groups so shared-memory reads are 128-bit
+// and conflict free), K in chunks of 16 staged by cp.async double buffering.
+#include <algorithm>
+
+#include "linac_host.h"
+#include "update.cuh"
+
+namespace linac {
+
+template <int FOLD>
+__global__ void __launch_bounds__(256, 1)
+update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, int c0, Field f,
+                    const DenseState* __restrict__ st, const int32_t* __restrict__ Ft, int64_t ldF,
+                    const int32_t* __restrict__ R, int64_t ldR) {
+    static_assert(UPD_BK % FOLD == 0, "fold cadence must divide the K chunk");
+    __shared__ __align__(16) int32_t As[2][UPD_BK][UPD_BM];
+    __shared__ __align__(16) int32_t Bs[2][UPD_BK][UPD_BN];
+    const int k = st->k;
+    if (k == 0) return;
+    const int r = st->r;
+    const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
+    const int64_t row0 = (int64_t)blockIdx.y * UPD_BM;
+    const int64_t col0 = (int64_t)blockIdx.x * UPD_BN;   // relative to c0
+    const int64_t ncols = n - c0;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+
+    auto load = [&](int stage, int k0) {
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            const int c = tid + it * 256;
+            const int kk = c >> 5, x4 = (c & 31) * 4;
+            {
+                const int64_t row = row0 + x4;
+                const int bytes = row + 4 <= m ? 16 : (row < m ? (int)(m - row) * 4 : 0);
+                const int32_t* src = bytes ? Ft + (int64_t)(k0 + kk) * ldF + row : Ft;
+                cp_async16(&As[stage][kk][x4], src, bytes);
+            }
+            {
+                const int64_t col = col0 + x4;
+                const int bytes = col + 4 <= ncols ? 16 : (col < ncols ? (int)(ncols - col) * 4 : 0);
+                const int32_t* src = bytes ? R + (int64_t)(k0 + kk) * ldR + col : R;
+                cp_async16(&Bs[stage][kk][x4], src, bytes);
+            }
+        }
+        cp_async_commit();
+    };
+
+    int64_t acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0;
+
+    const int nk = kpad / UPD_BK;
+    load(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        if (kt + 1 < nk) {
+            load((kt + 1) & 1, (kt + 1) * UPD_BK);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int s = kt & 1;
+#pragma unroll
+        for (int kk = 0; kk < UPD_BK; ++kk) {
+            const int4 a0 = *reinterpret_cast<const int4*>(&As[s][kk][ty * 4]);
+            const int4 a1 = *reinterpret_cast<const int4*>(&As[s][kk][64 + ty * 4]);
+            const int4 b0 = *reinterpret_cast<const int4*>(&Bs[s][kk][tx * 4]);
+            const int4 b1 = *reinterpret_cast<const int4*>(&Bs[s][kk][64 + tx * 4]);
+            const int a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const int b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += (int64_t)a[i] * (int64_t)b[j];
+            if ((kk + 1) % FOLD == 0) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fold64(acc[i][j], f);
+            }
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t row = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (row >= m) continue;
+        const bool pivot_row = row >= r && row < r + k;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t col = col0 + h * 64 + tx * 4;
+            if (col >= ncols) continue;
+            uint32_t* dst = M + row * ld + c0 + col;
+            uint32_t out[4];
+            if (pivot_row) {
+                const int32_t* rr = R + (int64_t)(row - r) * ldR + col;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) out[q] = col + q < ncols ? from_balanced(rr[q], f) : 0u;
+            } else if (col + 4 <= ncols) {
+                const uint4 cv = *reinterpret_cast<const uint4*>(dst);
+                const uint32_t c4[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) out[q] = submod(c4[q], reduce_signed(acc[i][h * 4 + q], f), f);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    out[q] = col + q < ncols ? submod(dst[q], reduce_signed(acc[i][h * 4 + q], f), f) : 0u;
+            }
+            if (col + 4 <= ncols) {
+                *reinterpret_cast<uint4*>(dst) = make_uint4(out[0], out[1], out[2], out[3]);
+            } else {
+                for (int q = 0; q < 4 && col + q < ncols; ++q) dst[q] = out[q];
+            }
+        }
+    }
+}
+
+linac_status launch_update_limb(uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0, const Field& f,
+                                const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,
+                                int64_t ldR, const LimbScratch* limb, cudaStream_t stream);
+
+linac_status launch_update(int path, uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0,
+                           const Field& f, const DenseState* st, const int32_t* Ft, int64_t ldF,
+                           const int32_t* R, int64_t ldR, const LimbScratch* limb,
+                           cudaStream_t stream) {
+    if (path == LINAC_PATH_LIMB)
+        return launch_update_limb(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, limb, stream);
+    const int64_t ncols = n - c0;
+    if (ncols <= 0 || m <= 0) return LINAC_OK;
+    dim3 grid((unsigned)((ncols + UPD_BN - 1) / UPD_BN), (unsigned)((m + UPD_BM - 1) / UPD_BM));
+    if (f.fold >= 16)
+        update_plain_kernel<16><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR);
+    else if (f.fold >= 8)
+        update_plain_kernel<8><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR);
+    else
+        update_plain_kernel<4><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR);
+    LINAC_CUDA_TRY(cudaGetLastError());
+    return LINAC_OK;
+}
+
+}  // namespace linac

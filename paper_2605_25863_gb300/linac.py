@@ -1,0 +1,197 @@
+"""Thin ctypes binding of the C ABI in include/linac.h.
+
+Every function marshals torch CUDA tensors into device pointers, calls the
+entry point of the same name in liblinac.so and turns a nonzero status into
+``LinacError``.  There is no fallback: if the library is missing, every call
+raises.  Matrices are 2-D int32 (or uint32) CUDA tensors holding residues in
+[0, p), row-major with a row stride that is a multiple of 4 elements.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+LINAC_PATH_AUTO, LINAC_PATH_PLAIN, LINAC_PATH_LIMB = 0, 1, 2
+LINAC_SHARED_PATTERN = 1
+_PATHS = {"auto": LINAC_PATH_AUTO, "plain": LINAC_PATH_PLAIN, "limb": LINAC_PATH_LIMB}
+
+
+class LinacError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        name = lib().linac_status_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: status {code} ({name})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("nb", ctypes.c_int32),
+                ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load liblinac.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+        L.linac_rref.argtypes = [vp, i64, i64, i64, u32, vp, vp, vp]
+        L.linac_rref_ex.argtypes = [vp, i64, i64, i64, u32, i64, vp, vp, ctypes.POINTER(Options), vp]
+        L.linac_solve.argtypes = [vp, i64, i64, i64, vp, i64, i64, u32, vp, i64, vp, vp, vp, vp]
+        L.linac_solve_ex.argtypes = [vp, i64, i64, i64, vp, i64, i64, u32, vp, i64, vp, vp, vp,
+                                     ctypes.POINTER(Options), vp]
+        L.linac_rref_batched.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, i32, u32, u32, vp, vp, vp,
+                                         vp, vp]
+        L.linac_workspace_bytes.argtypes = [i64, i64, ctypes.POINTER(Options)]
+        L.linac_workspace_bytes.restype = ctypes.c_size_t
+        L.linac_last_device_status.argtypes = [vp]
+        L.linac_status_string.argtypes = [ctypes.c_int]
+        L.linac_status_string.restype = ctypes.c_char_p
+        L.linac_version.argtypes = []
+        for name in ("linac_rref", "linac_rref_ex", "linac_solve", "linac_solve_ex",
+                     "linac_rref_batched", "linac_last_device_status", "linac_version"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def header_symbols() -> list[str]:
+    """Entry points declared in include/linac.h."""
+    hdr = os.path.join(os.path.dirname(_build.HERE), "include", "linac.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(linac_\w+)\s*\(", text, re.M)))
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise LinacError(code, where)
+
+
+def _matrix(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or t.dim() != 2 or not t.is_cuda:
+        raise ValueError(f"{name} must be a 2-D CUDA tensor")
+    if t.dtype not in (torch.int32, torch.uint32):
+        raise ValueError(f"{name} must be int32 or uint32")
+    if t.stride(1) != 1 and t.shape[1] > 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+    ld = t.stride(0) if t.shape[0] > 1 else max(t.shape[1] + (-t.shape[1]) % 4, 4)
+    return t.data_ptr(), t.shape[0], t.shape[1], ld
+
+
+def _opts(path="auto", nb=0, validate=False) -> Options:
+    return Options(_PATHS[path] if isinstance(path, str) else int(path), int(nb), int(bool(validate)), 0)
+
+
+def padded(rows: int, cols: int, device="cuda") -> torch.Tensor:
+    """A zeroed rows x cols int32 view whose row stride is a multiple of 4."""
+    ld = max(cols + (-cols) % 4, 4)
+    return torch.zeros((rows, ld), dtype=torch.int32, device=device)[:, :cols]
+
+
+def to_device(M, device="cuda") -> torch.Tensor:
+    """Copy a host matrix of residues into a padded int32 device view."""
+    import numpy as np
+    M = np.ascontiguousarray(np.asarray(M, dtype=np.uint32))
+    out = padded(M.shape[0], M.shape[1], device)
+    out.copy_(torch.from_numpy(M.view(np.int32)))
+    return out
+
+
+def linac_rref(A: torch.Tensor, p: int, *, ncols_search: int | None = None, path="auto", nb: int = 0,
+               validate: bool = False, stream=None):
+    """In-place RREF of A (paper section 3.2).  Returns (rank, pivots) as int32
+    CUDA tensors (rank has one element; pivots has min(m, ncols_search)
+    entries, -1 after the rank)."""
+    ptr, m, n, ld = _matrix(A, "A")
+    ns = n if ncols_search is None else int(ncols_search)
+    rank = torch.zeros(1, dtype=torch.int32, device=A.device)
+    piv = torch.full((max(min(m, ns), 1),), -1, dtype=torch.int32, device=A.device)
+    o = _opts(path, nb, validate)
+    _check(lib().linac_rref_ex(ptr, m, n, ld, p, ns, rank.data_ptr(), piv.data_ptr(), ctypes.byref(o),
+                               _stream_ptr(stream)), "linac_rref")
+    return rank, piv[:min(m, ns)]
+
+
+def linac_solve(A: torch.Tensor, B: torch.Tensor, p: int, *, path="auto", nb: int = 0,
+                validate: bool = False, stream=None):
+    """Particular solutions of A X = B (paper section 5.2).  Returns
+    (X, consistent, rank, pivots) as CUDA tensors; A and B are not modified."""
+    pa, m, nA, ldA = _matrix(A, "A")
+    pb, mb, k, ldB = _matrix(B, "B")
+    if mb != m:
+        raise ValueError("A and B need the same number of rows")
+    X = torch.zeros((max(nA, 1), max(k, 1)), dtype=torch.int32, device=A.device)
+    cons = torch.zeros(max(k, 1), dtype=torch.uint8, device=A.device)
+    rank = torch.zeros(1, dtype=torch.int32, device=A.device)
+    piv = torch.full((max(min(m, nA), 1),), -1, dtype=torch.int32, device=A.device)
+    o = _opts(path, nb, validate)
+    _check(lib().linac_solve_ex(pa, m, nA, ldA, pb, k, ldB, p, X.data_ptr(), X.stride(0), cons.data_ptr(),
+                                rank.data_ptr(), piv.data_ptr(), ctypes.byref(o), _stream_ptr(stream)),
+           "linac_solve")
+    return X[:nA, :k], cons[:k].bool(), rank, piv[:min(m, nA)]
+
+
+def linac_rref_batched(data: torch.Tensor, offsets: torch.Tensor, m: torch.Tensor, n: torch.Tensor,
+                       ld: torch.Tensor, p: int, *, nsearch: torch.Tensor | None = None, flags: int = 0,
+                       max_m: int | None = None, max_n: int | None = None, stream=None):
+    """In-place RREF of a packed batch of systems (see include/linac.h).
+    Returns (ranks, pivots, piv_offsets, status) as CUDA tensors."""
+    dev = data.device
+    batch = int(m.numel())
+    mm = m.to(torch.int64)
+    nn = (nsearch if nsearch is not None else n).to(torch.int64)
+    npiv = torch.minimum(mm, nn)
+    piv_off = torch.zeros(batch, dtype=torch.int64, device=dev)
+    if batch > 1:
+        piv_off[1:] = torch.cumsum(npiv, 0)[:-1]
+    total = int(npiv.sum().item()) if batch else 0
+    pivots = torch.full((max(total, 1),), -1, dtype=torch.int32, device=dev)
+    ranks = torch.zeros(max(batch, 1), dtype=torch.int32, device=dev)
+    status = torch.zeros(max(batch, 1), dtype=torch.int32, device=dev)
+    if max_m is None:
+        max_m = int(m.max().item()) if batch else 0
+    if max_n is None:
+        max_n = int(n.max().item()) if batch else 0
+    _check(lib().linac_rref_batched(data.data_ptr(), offsets.data_ptr(), m.data_ptr(), n.data_ptr(),
+                                    ld.data_ptr(), nsearch.data_ptr() if nsearch is not None else None,
+                                    batch, int(max_m), int(max_n), p, flags, ranks.data_ptr(),
+                                    pivots.data_ptr(), piv_off.data_ptr(), status.data_ptr(),
+                                    _stream_ptr(stream)), "linac_rref_batched")
+    return ranks[:batch], pivots, piv_off, status[:batch]
+
+
+def linac_last_device_status(stream=None) -> int:
+    return int(lib().linac_last_device_status(_stream_ptr(stream)))
+
+
+def linac_workspace_bytes(m: int, n: int, nb: int = 0) -> int:
+    o = _opts("auto", nb, False)
+    return int(lib().linac_workspace_bytes(m, n, ctypes.byref(o)))
+
+
+def linac_version() -> int:
+    return int(lib().linac_version())

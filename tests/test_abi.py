@@ -1,0 +1,71 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point
+that include/linac.h declares, and rejects bad arguments on the host
+(argument checks run before any CUDA call)."""
+import ctypes
+
+import pytest
+
+from paper_2605_25863_gb300 import build, linac
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return linac.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = linac.header_symbols()
+    assert {"linac_rref", "linac_solve", "linac_rref_batched", "linac_workspace_bytes"} <= set(syms)
+    for s in syms:
+        assert hasattr(lib, s), f"{s} declared in include/linac.h but not exported"
+
+
+def test_build_targets_sm_103a_only():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_status_strings_and_version(lib):
+    assert lib.linac_version() >= 100
+    for code in range(9):
+        assert lib.linac_status_string(code)
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 4, 9, 561, 2047, 3277, 4033, 25326001, 2**31, 2**31 + 11,
+                               2**32 - 1, 2**31 - 3])
+def test_non_primes_and_out_of_range_primes_rejected(lib, p):
+    rank = ctypes.c_int32()
+    piv = (ctypes.c_int32 * 4)()
+    code = lib.linac_rref(None, 0, 0, 4, p, ctypes.byref(rank), piv, None)
+    assert code == 2   # LINAC_ERR_PRIME
+
+
+@pytest.mark.parametrize("m,n,ld,code", [(-1, 4, 4, 1), (4, -1, 4, 1), (4, 8, 4, 1), (4, 5, 6, 3)])
+def test_shape_and_alignment_rejected(lib, m, n, ld, code):
+    rank = ctypes.c_int32()
+    piv = (ctypes.c_int32 * 8)()
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: rejected before any CUDA call
+    assert lib.linac_rref(fake, m, n, ld, 2**31 - 1, ctypes.byref(rank), piv, None) == code
+
+
+def test_misaligned_pointer_rejected(lib):
+    rank = ctypes.c_int32()
+    piv = (ctypes.c_int32 * 8)()
+    assert lib.linac_rref(ctypes.c_void_p(0x1004), 4, 4, 4, 2**31 - 1, ctypes.byref(rank), piv, None) == 3
+
+
+def test_bad_options_rejected(lib):
+    rank = ctypes.c_int32()
+    piv = (ctypes.c_int32 * 8)()
+    for path, nb in ((3, 0), (-1, 0), (0, 20), (0, 256)):
+        o = linac.Options(path, nb, 0, 0)
+        assert lib.linac_rref_ex(ctypes.c_void_p(0x1000), 4, 4, 4, 2**31 - 1, 4, ctypes.byref(rank), piv,
+                                 ctypes.byref(o), None) == 1
+
+
+def test_batched_rejects_oversize(lib):
+    code = lib.linac_rref_batched(ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000),
+                                  ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000), None, 3, 10, 2000,
+                                  2**31 - 1, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000),
+                                  ctypes.c_void_p(0x1000), None, None)
+    assert code == 8   # LINAC_ERR_UNSUPPORTED
