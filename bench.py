@@ -1,0 +1,471 @@
+#!/usr/bin/env python
+"""Benchmark of exact mod-p Gauss-Jordan elimination to RREF on GB300.
+
+Headline workload: the dense 32768 x 33024 system over F_p, p = 2^31 - 1
+(A 32768 x 32768 plus 256 right-hand-side columns, uniform residues, full
+rank), reduced in place by linac_rref.  One step = one complete RREF.
+Metric: field multiply-adds per second, counted as the Gauss-Jordan work
+W = sum over pivots t of (m - 1) * (n - c_t - 1), the multiply-adds the
+paper's column-by-column elimination performs (section 3.2), whatever the
+blocking.
+
+Timing: W >= 3 untimed warm-up steps, then K timed steps bracketed by a
+barrier and torch.cuda.synchronize(); every step restores the pristine input
+with a full device copy (4.3 GB, larger than L2) outside its CUDA events, so
+each timed elimination starts from cold L2.  With --gpus N under torchrun
+every rank reduces its own copy (replicas; the elimination of one matrix
+does not shard) and value = total work / max rank time.
+
+Also reported: the dominant kernel's roofline (CUDA events around each of
+its launches, on the launch stream), the e2e rate through the public API
+with host buffers (pinned H2D, RREF, D2H each step), the CPU oracle on a
+bounded sample of the same workload, the u8-limb tensor path beside the
+plain path, the batched workload (systems/s) and the shared-pattern batch.
+
+--impl reference times the CPU oracle alone (rank 0), on bounded samples of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "mod-p MACs/s for RREF at n=32768 (tensor vs plain path); batched systems/s"
+UNIT = "field MAC/s"
+P31 = 2**31 - 1
+SMS = 152                 # GB300 SM count
+SM_MAX_MHZ = 2070.0       # GB300 maximum SM clock
+IMAD_LANES_PER_SM = 64    # 32-bit integer multiply-add lanes per SM per clock (4 x 16)
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--m", type=int, default=32768, help="rows (= unknowns) of the dense system")
+    ap.add_argument("--rhs", type=int, default=256, help="right-hand-side columns")
+    ap.add_argument("--nb", type=int, default=128, help="panel width")
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "limb"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the CPU oracle, path comparison and batched legs")
+    ap.add_argument("--batch-count", type=int, default=10000)
+    return ap.parse_args()
+
+
+def gj_work(m: int, n: int, pivots) -> int:
+    """Field multiply-adds of Gauss-Jordan elimination: sum_t (m-1)(n-c_t-1)."""
+    piv = np.asarray(pivots, dtype=np.int64)
+    return int(((m - 1) * (n - piv - 1)).sum())
+
+
+def update_work(m: int, n: int, pivots, nb: int) -> int:
+    """Useful multiply-adds of the blocked trailing updates: per panel starting
+    at c0 with k pivots, (m - k) rows x (n - c0) columns x k."""
+    piv = np.asarray(pivots, dtype=np.int64)
+    total = 0
+    for c0 in range(0, n, nb):
+        k = int(((piv >= c0) & (piv < c0 + nb)).sum())
+        total += (m - k) * (n - c0) * k
+    return total
+
+
+def workload_name(m, n, rhs):
+    return (f"dense RREF over F_p, p = 2^31 - 1: {m} x {n} (A {m} x {m} plus {rhs} right-hand "
+            f"sides), uniform residues, full rank")
+
+
+def fold_of(p: int) -> int:
+    c32 = (1 << 32) % p
+    half = (p - 1) // 2
+    amax = max(((1 << 31) - 1) * c32 + (1 << 32) - 1, (1 << 31) * c32)
+    f = ((1 << 63) - 1 - amax) // (half * half)
+    return 16 if f >= 16 else (8 if f >= 8 else 4)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.lines: list[str] = []
+        self.err = None
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if gpu_id:
+                cmd.insert(1, f"--id={gpu_id}")
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception as e:  # nvidia-smi missing
+            self.proc = None
+            self.err = str(e)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"error": self.err}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"error": "no samples", "samples": len(self.lines)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "sm_mhz_min": min(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the workload
+
+def cpu_oracle_sample(M: np.ndarray, p: int, budget_s: float, cores: int):
+    """Time the oracle on the first P pivot steps of M (P sized to the
+    budget).  Returns (rate, seconds, P, macs)."""
+    import oracle
+    m, n = M.shape
+    t0 = time.perf_counter()
+    _, r, piv, _ = oracle.rref(M, p, max_pivots=1, nthreads=cores)
+    t1 = time.perf_counter() - t0
+    P = max(1, min(m, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    _, r, piv, _ = oracle.rref(M, p, max_pivots=P, nthreads=cores)
+    dt = time.perf_counter() - t0
+    macs = gj_work(m, n, piv)
+    return macs / dt, dt, int(r), macs
+
+
+def host_matrix(m: int, n: int, p: int, seed: int = 5) -> np.ndarray:
+    from paper_2605_25863_gb300 import synth
+    import torch
+    t = synth.uniform_torch(m, n, p, synth.stream_key(seed, "large_dense"), device="cpu")
+    return t.numpy().view(np.uint32)
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    m, n = args.m, args.m + args.rhs
+    cores = os.cpu_count() or 1
+    M = host_matrix(m, n, P31)
+    steps, warm = args.steps, args.warmup
+    per_step = max(2.0, 120.0 / max(1, steps + warm))
+    for _ in range(warm):
+        cpu_oracle_sample(M, P31, per_step, cores)
+    rates, secs, samples = [], [], []
+    for _ in range(steps):
+        rate, dt, P, macs = cpu_oracle_sample(M, P31, per_step, cores)
+        rates.append(rate)
+        secs.append(dt)
+        samples.append(P)
+    value = float(sum(r * s for r, s in zip(rates, secs)) / sum(secs))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * sum(secs) / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(m, n, args.rhs), "m": m, "n": n, "p": P31},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {samples} pivot steps (of {m}) of the {m} x {n} elimination "
+                                   f"per step, {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_25863_gb300 import linac, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    m, rhs = args.m, args.rhs
+    n = m + rhs
+    p = P31
+    nb = args.nb
+    key = synth.stream_key(5, "large_dense")
+    pristine = synth.uniform_torch(m, n, p, key, device=dev)          # int32 view of the residues
+    work = torch.empty_like(pristine)
+
+    def step(path=args.path):
+        work.copy_(pristine)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r, piv = linac.linac_rref(work, p, nb=nb, path=path)
+        e1.record(stream)
+        return e0, e1, r, piv
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    linac.linac_profile_reset()
+    linac.linac_profile_enable(True)
+    launches0 = linac.linac_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    events = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    launches = linac.linac_launch_count() - launches0
+    clocks = sampler.stop()
+    linac.linac_profile_enable(False)
+    prof = linac.linac_profile_read()
+
+    step_ms = [a.elapsed_time(b) for a, b, _, _ in events]
+    rank_v = int(events[-1][2].item())
+    piv = events[-1][3].cpu().numpy()[:rank_v]
+    ok = rank_v == m and np.array_equal(piv, np.arange(m))
+    work_macs = gj_work(m, n, piv)
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * work_macs * args.steps / (tot_ms / 1000.0)
+
+    # dominant kernel: the trailing update
+    upd_name = "update_limb" if args.path == "limb" else "update_plain"
+    upd_launches, upd_ms = prof.get(upd_name, (0, 0.0))
+    upd_macs = update_work(m, n, piv, nb) * args.steps
+    fold = fold_of(p)
+    imad_per_mac = 1.0 + 2.0 / fold
+    achieved = upd_macs / (upd_ms / 1000.0) if upd_ms else 0.0
+    peak = SMS * IMAD_LANES_PER_SM * SM_MAX_MHZ * 1e6 / imad_per_mac
+    kernel_times = {k: {"launches": v[0], "total_ms": round(v[1], 3),
+                        "share": round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4)}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_name(m, n, rhs), "m": m, "n": n, "p": p, "nb": nb,
+                   "path": args.path, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "input 4.3 GB > L2, restored by a full device copy before every step"
+                         if m == 32768 else "input restored by a full device copy before every step"},
+        "roofline": {"kernel": upd_name, "bound": "alu", "achieved": achieved / 1e12,
+                     "peak": peak / 1e12, "unit": "Tfield-MAC/s", "frac": achieved / peak if peak else None,
+                     "traffic": None,
+                     "peak_basis": f"{SMS} SMs x {IMAD_LANES_PER_SM} IMAD/clk x {SM_MAX_MHZ:.0f} MHz / "
+                                   f"{imad_per_mac:.3f} IMAD per field MAC (fold every {fold})",
+                     "avg_launch_ms": upd_ms / max(1, upd_launches), "launches": upd_launches},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "correct": bool(ok),
+        "wall_s_timed": t_wall,
+        "kernel_times": kernel_times,
+    }
+
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = e2e_leg(args, linac, synth, pristine, work, m, n, p, nb, stream)
+        line["paths"] = path_leg(args, linac, pristine, work, m, n, p, nb, stream, value)
+        if world == 1:
+            line["cpu_baseline"] = cpu_leg(args, pristine, m, n, p)
+        line["batched"] = batched_leg(args, linac, synth, dev, stream)
+        line["shared_pattern"] = shared_leg(args, linac, synth, dev, stream)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_leg(args, linac, synth, pristine, work, m, n, p, nb, stream):
+    """Through the public API with host buffers: pinned H2D of the input, the
+    RREF, D2H of the reduced matrix and of rank/pivots, every step."""
+    import torch
+    host_in = torch.empty(pristine.shape, dtype=torch.int32, pin_memory=True)
+    host_in.copy_(pristine)
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        work.copy_(host_in, non_blocking=True)
+        r, piv = linac.linac_rref(work, p, nb=nb, path=args.path)
+        host_out.copy_(work, non_blocking=True)
+        rk = r.to("cpu", non_blocking=True)
+        pv = piv.to("cpu", non_blocking=True)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    macs = gj_work(m, n, pv.numpy()[:int(rk.item())])
+    nbytes = host_in.numel() * 4
+    return {"value": macs * steps / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes + 4 + 4 * m, "steps": steps, "ms_per_step": 1000 * dt / steps}
+
+
+def path_leg(args, linac, pristine, work, m, n, p, nb, stream, main_value):
+    """Plain CUDA-core update vs u8-limb integer-tensor update, one timed
+    elimination each (after one warm-up)."""
+    import torch
+    out = {}
+    for path in ("plain", "limb"):
+        try:
+            for it in range(2):
+                work.copy_(pristine)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r, piv = linac.linac_rref(work, p, nb=nb, path=path)
+                e1.record(stream)
+                torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rk = int(r.item())
+            macs = gj_work(m, n, piv.cpu().numpy()[:rk])
+            out[path] = {"value": macs / (ms / 1000.0), "ms": ms, "correct": rk == m}
+        except Exception as e:  # a path that is not available reports why
+            out[path] = {"error": str(e)}
+    if "value" in out.get("plain", {}) and "value" in out.get("limb", {}):
+        out["limb_over_plain"] = out["limb"]["value"] / out["plain"]["value"]
+    return out
+
+
+def cpu_leg(args, pristine, m, n, p):
+    cores = os.cpu_count() or 1
+    M = pristine.cpu().numpy().view(np.uint32)
+    rate, dt, P, macs = cpu_oracle_sample(M, p, args.cpu_seconds, cores)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {P} pivot steps (of {m}) of the same {m} x {n} elimination "
+                      f"({macs:.3e} field MACs, {dt:.1f} s, {cores} threads)"}
+
+
+def batched_leg(args, linac, synth, dev, stream):
+    """10,000 uneven systems [A | B] (n log-uniform in [32, 512], 4 RHS, 10 %
+    rank-deficient), one linac_rref_batched call per step."""
+    import torch
+    B = synth.batched_uneven(count=args.batch_count)
+    data0 = torch.from_numpy(B.data.view(np.int32)).to(dev)
+    data = torch.empty_like(data0)
+    offs = torch.from_numpy(B.offsets).to(dev)
+    mm = torch.from_numpy(B.m).to(dev)
+    nn = torch.from_numpy(B.n).to(dev)
+    ld = torch.from_numpy(B.ld).to(dev)
+    ns = torch.from_numpy(B.nA).to(dev)
+    times = []
+    for it in range(4):
+        data.copy_(data0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ranks, piv, poff, st = linac.linac_rref_batched(data, offs, mm, nn, ld, B.p, nsearch=ns,
+                                                        max_m=int(B.m.max()), max_n=int(B.n.max()))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    rk = ranks.cpu().numpy()
+    ok = bool((rk == B.nA - B.deficiency).all())
+    macs = sum((int(B.m[s]) - 1) * (int(B.n[s]) * int(rk[s]) - int(rk[s]) * (int(rk[s]) + 1) // 2)
+               for s in range(B.count))
+    return {"systems": B.count, "systems_per_s": B.count / (ms / 1000.0), "ms": ms,
+            "field_macs_per_s_approx": macs / (ms / 1000.0), "ranks_ok": ok,
+            "workload": "batched uneven [A|B], n log-uniform [32,512], 4 RHS, p = 2^31 - 19"}
+
+
+def shared_leg(args, linac, synth, dev, stream):
+    """4096 evaluations of a 384 x 400 block-banded polynomial template."""
+    import torch
+    B = synth.shared_pattern(count=4096)
+    data0 = torch.from_numpy(B.data.view(np.int32)).to(dev)
+    data = torch.empty_like(data0)
+    offs = torch.from_numpy(B.offsets).to(dev)
+    mm = torch.from_numpy(B.m).to(dev)
+    nn = torch.from_numpy(B.n).to(dev)
+    ld = torch.from_numpy(B.ld).to(dev)
+    ns = torch.from_numpy(B.nA).to(dev)
+    out = {}
+    for name, flags in (("search", 0), ("shared_pattern", linac.LINAC_SHARED_PATTERN)):
+        times = []
+        for it in range(3):
+            data.copy_(data0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ranks, piv, poff, st = linac.linac_rref_batched(data, offs, mm, nn, ld, B.p, nsearch=ns,
+                                                            flags=flags, max_m=384, max_n=400)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it:
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        out[name] = {"systems_per_s": B.count / (ms / 1000.0), "ms": ms,
+                     "ranks_ok": bool((ranks.cpu().numpy() == 384).all())}
+    out["speedup"] = out["search"]["ms"] / out["shared_pattern"]["ms"]
+    return out
+
+
+def main():
+    args = parse()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps; the number is not a valid bench value", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

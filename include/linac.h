@@ -164,6 +164,23 @@ linac_status linac_last_device_status(cudaStream_t stream);
 /* Human-readable name of a status code (static string). */
 const char *linac_status_string(linac_status s);
 
+/* Profiling.  When enabled, every kernel launch of the library is bracketed
+ * by CUDA events recorded on its own stream, accumulated per kernel class
+ * ("panel", "trsm", "update_plain", ...).  linac_profile_read synchronises
+ * the recorded events and fills up to max_entries entries (classes with at
+ * least one timed launch), returning how many were written.  Launches are
+ * counted whether or not profiling is enabled. */
+typedef struct {
+    const char *name;      /* static string */
+    long long launches;
+    double total_ms;
+} linac_profile_entry;
+
+void linac_profile_enable(int on);
+void linac_profile_reset(void);
+int linac_profile_read(linac_profile_entry *out, int max_entries);
+long long linac_launch_count(void);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t linac_version(void);
 

@@ -10,6 +10,7 @@
 #include <climits>
 
 #include "linac_host.h"
+#include "profile.h"
 
 namespace linac {
 
@@ -106,6 +107,7 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
     unsigned int* counter = (unsigned int*)buf;
     LINAC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned int), stream));
     const int grid = std::max(1, std::min(batch, sm_count() * 8));
+    ProfScope ps(stream, PROF_BATCHED);
     batched_gj_kernel<<<grid, BATCH_THREADS, 0, stream>>>(d_data, d_offsets, d_m, d_n, d_ld, d_nsearch, batch, f,
                                                           d_ranks, d_pivots, d_piv_offsets, d_status, counter);
     LINAC_CUDA_TRY(cudaGetLastError());

@@ -34,6 +34,7 @@
 #include <cstdio>
 
 #include "linac_host.h"
+#include "profile.h"
 #include "update.cuh"
 
 namespace linac {
@@ -483,6 +484,7 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
     }
     {
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((npiv + 255) / 256, 1024));
+        ProfScope ps(stream, PROF_INIT);
         init_kernel<<<(unsigned)blocks, 256, 0, stream>>>(st, d_pivots, npiv, d_rank);
         LINAC_CUDA_TRY(cudaGetLastError());
     }
@@ -497,22 +499,39 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
             int c0_ = (int)c0, w_ = w, S_ = S_max;
             Field f_ = f;
             void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status};
+            ProfScope ps(stream, PROF_PANEL);
             LINAC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_kernel, dim3(G), dim3(PANEL_THREADS),
                                                        args, psmem, stream));
         }
-        gather_f_kernel<<<(unsigned)((m + 63) / 64), 256, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, Ft, L.ldF);
+        {
+            ProfScope ps(stream, PROF_GATHER_F);
+            gather_f_kernel<<<(unsigned)((m + 63) / 64), 256, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, Ft, L.ldF);
+        }
         {
             const unsigned gx = (unsigned)std::min<int64_t>((ncols + 1023) / 1024, 64);
+            ProfScope ps(stream, PROF_GATHER_W);
             gather_w_kernel<<<dim3(std::max(1u, gx), NB_MAX), 256, 0, stream>>>(dA, ld, ncols, (int)c0, st, W, L.ldW);
         }
-        heads_inverse_kernel<<<1, NB_MAX, 0, stream>>>(st, panelU, (int)c0, f.p, status);
-        trsm_kernel<<<(unsigned)((ncols + TRSM_TB - 1) / TRSM_TB), 256, tsmem, stream>>>(
-            W, L.ldW, ncols, (int)c0, f, st, panelU, R, L.ldW);
-        move_kernel<<<NB_MAX, 256, 0, stream>>>(dA, ld, n, (int)c0, st, Ft, L.ldF);
+        {
+            ProfScope ps(stream, PROF_INVERSE);
+            heads_inverse_kernel<<<1, NB_MAX, 0, stream>>>(st, panelU, (int)c0, f.p, status);
+        }
+        {
+            ProfScope ps(stream, PROF_TRSM);
+            trsm_kernel<<<(unsigned)((ncols + TRSM_TB - 1) / TRSM_TB), 256, tsmem, stream>>>(
+                W, L.ldW, ncols, (int)c0, f, st, panelU, R, L.ldW);
+        }
+        {
+            ProfScope ps(stream, PROF_MOVE);
+            move_kernel<<<NB_MAX, 256, 0, stream>>>(dA, ld, n, (int)c0, st, Ft, L.ldF);
+        }
         linac_status us = launch_update(path, dA, m, n, ld, (int)c0, f, st, Ft, L.ldF, R, L.ldW,
                                        limb_ok ? &limb : nullptr, stream);
         if (us != LINAC_OK) return us;
-        finish_kernel<<<1, NB_MAX, 0, stream>>>(st, d_pivots, d_rank);
+        {
+            ProfScope ps(stream, PROF_FINISH);
+            finish_kernel<<<1, NB_MAX, 0, stream>>>(st, d_pivots, d_rank);
+        }
         LINAC_CUDA_TRY(cudaGetLastError());
     }
     return LINAC_OK;
@@ -523,6 +542,7 @@ linac_status solve_pack(const uint32_t* dA, int64_t m, int64_t nA, int64_t ldA, 
     if (m == 0) return LINAC_OK;
     const int64_t total = m * ldM;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096));
+    ProfScope ps(stream, PROF_SOLVE_PACK);
     pack_kernel<<<blocks, 256, 0, stream>>>(dA, m, nA, ldA, dB, k, ldB, dM, ldM);
     LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;
@@ -532,6 +552,7 @@ linac_status solve_extract(const uint32_t* dM, int64_t m, int64_t nA, int64_t k,
                            const int32_t* d_rank, const int32_t* d_pivots, uint32_t* dX, int64_t ldX,
                            uint8_t* d_consistent, cudaStream_t stream) {
     if (k == 0) return LINAC_OK;
+    ProfScope ps(stream, PROF_SOLVE_EXTRACT);
     extract_kernel<<<(unsigned)k, 256, 0, stream>>>(dM, m, nA, ldM, d_rank, d_pivots, dX, ldX, d_consistent);
     LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;
@@ -541,6 +562,7 @@ linac_status validate_range(const uint32_t* dA, int64_t m, int64_t n, int64_t ld
                             int* d_status, cudaStream_t stream) {
     if (m == 0 || n == 0) return LINAC_OK;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((m * n + 255) / 256, 4096));
+    ProfScope ps(stream, PROF_VALIDATE);
     validate_kernel<<<blocks, 256, 0, stream>>>(dA, m, n, ld, p, d_status);
     LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "linac_host.h"
+#include "profile.h"
 #include "update.cuh"
 
 namespace linac {
@@ -144,6 +145,7 @@ linac_status launch_update(int path, uint32_t* M, int64_t m, int64_t n, int64_t 
     const int64_t ncols = n - c0;
     if (ncols <= 0 || m <= 0) return LINAC_OK;
     dim3 grid((unsigned)((ncols + UPD_BN - 1) / UPD_BN), (unsigned)((m + UPD_BM - 1) / UPD_BM));
+    ProfScope ps(stream, PROF_UPDATE_PLAIN);
     if (f.fold >= 16)
         update_plain_kernel<16><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR);
     else if (f.fold >= 8)

@@ -37,6 +37,10 @@ class Options(ctypes.Structure):
                 ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -66,6 +70,14 @@ def lib():
         L.linac_status_string.argtypes = [ctypes.c_int]
         L.linac_status_string.restype = ctypes.c_char_p
         L.linac_version.argtypes = []
+        L.linac_profile_enable.argtypes = [ctypes.c_int]
+        L.linac_profile_enable.restype = None
+        L.linac_profile_reset.argtypes = []
+        L.linac_profile_reset.restype = None
+        L.linac_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), ctypes.c_int]
+        L.linac_profile_read.restype = ctypes.c_int
+        L.linac_launch_count.argtypes = []
+        L.linac_launch_count.restype = ctypes.c_longlong
         for name in ("linac_rref", "linac_rref_ex", "linac_solve", "linac_solve_ex",
                      "linac_rref_batched", "linac_last_device_status", "linac_version"):
             getattr(L, name).restype = ctypes.c_int
@@ -195,3 +207,22 @@ def linac_workspace_bytes(m: int, n: int, nb: int = 0) -> int:
 
 def linac_version() -> int:
     return int(lib().linac_version())
+
+
+def linac_profile_enable(on: bool = True):
+    lib().linac_profile_enable(1 if on else 0)
+
+
+def linac_profile_reset():
+    lib().linac_profile_reset()
+
+
+def linac_profile_read() -> dict:
+    """{kernel class: (launches, total_ms)} for the launches timed so far."""
+    buf = (ProfileEntry * 64)()
+    n = lib().linac_profile_read(buf, 64)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n)}
+
+
+def linac_launch_count() -> int:
+    return int(lib().linac_launch_count())
