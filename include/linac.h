@@ -88,6 +88,28 @@ typedef struct {
 linac_status linac_rref(uint32_t *d_A, int64_t m, int64_t n, int64_t ld, uint32_t p,
                         int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
 
+/*
+ * linac_rref_noalloc -- linac_rref for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant.
+ * linac_rref obtains its scratch with cudaMalloc on first use; callers whose
+ * own pool allocator owns the whole device, latency-critical loops that
+ * cannot absorb cudaMalloc's implicit synchronisation, and plugins hosted by
+ * processes that forbid foreign device allocations cannot allow that.  This
+ * entry point allocates nothing (with profiling off, the default): all
+ * scratch is one fixed 4 MiB device array inside the library, reserved on
+ * every device that loads it until the process exits.
+ *   Same arguments, results and errors as linac_rref (plain CUDA-core
+ *   update, default panel width), except:
+ *   - m <= 2048 and n <= 2048, otherwise LINAC_ERR_UNSUPPORTED;
+ *   - the first call on a device looks up the array's device address; make
+ *     it before any stream capture on that device;
+ *   - all calls share the array: calls that overlap on the GPU race and must
+ *     be serialised by the caller;
+ *   - device-side wait failures are not reported by linac_last_device_status.
+ */
+linac_status linac_rref_noalloc(uint32_t *d_A, int64_t m, int64_t n, int64_t ld, uint32_t p,
+                                int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
+
 /* linac_rref with options (NULL = defaults).  ncols_search limits the pivot
  * search to columns [0, ncols_search) while still reducing all n columns
  * (pass n for plain RREF). */

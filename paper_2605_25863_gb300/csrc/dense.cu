@@ -33,14 +33,12 @@
 #include <climits>
 #include <cstdio>
 
+#include "dense_kernels.cuh"
 #include "linac_host.h"
 #include "profile.h"
 #include "update.cuh"
 
 namespace linac {
-
-constexpr int PANEL_THREADS = 256;
-constexpr int TRSM_TB = 64;
 
 // ---------------------------------------------------------------------------
 // Initialisation and bookkeeping

@@ -1,0 +1,34 @@
+// dense_kernels.cuh -- declarations of the dense-elimination kernels defined
+// in dense.cu, with the launch constants they were written for.
+#pragma once
+#include <cstdint>
+
+#include "update.cuh"
+
+namespace linac {
+
+constexpr int PANEL_THREADS = 256;   // block size of panel_kernel
+constexpr int TRSM_TB = 64;          // columns per trsm_kernel block
+
+__global__ void init_kernel(DenseState* st, int32_t* d_pivots, int64_t npiv, int32_t* d_rank);
+__global__ void finish_kernel(DenseState* st, int32_t* d_pivots, int32_t* d_rank);
+__global__ void __launch_bounds__(PANEL_THREADS)
+panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, int S_max,
+             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status);
+__global__ void __launch_bounds__(256)
+gather_f_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f,
+                const DenseState* __restrict__ st, int32_t* __restrict__ Ft, int64_t ldF);
+__global__ void gather_w_kernel(const uint32_t* __restrict__ M, int64_t ld, int64_t ncols, int c0,
+                                const DenseState* __restrict__ st, uint32_t* __restrict__ W,
+                                int64_t ldW);
+__global__ void heads_inverse_kernel(DenseState* st, const uint32_t* __restrict__ panelU, int c0,
+                                     uint32_t p, int* status);
+__global__ void __launch_bounds__(256)
+trsm_kernel(const uint32_t* __restrict__ W, int64_t ldW, int64_t ncols, int c0, Field f,
+            const DenseState* __restrict__ st, const uint32_t* __restrict__ panelU,
+            int32_t* __restrict__ R, int64_t ldR);
+__global__ void __launch_bounds__(256)
+move_kernel(uint32_t* __restrict__ M, int64_t ld, int64_t n, int c0, const DenseState* __restrict__ st,
+            int32_t* __restrict__ Ft, int64_t ldF);
+
+}  // namespace linac
