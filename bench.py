@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU oracle, path comparison and batched legs")
     ap.add_argument("--batch-count", type=int, default=10000)
+    ap.add_argument("--measure-peaks", action="store_true",
+                    help="print the measured integer pipe rates (roofline denominators) and exit")
     return ap.parse_args()
 
 
@@ -464,6 +466,16 @@ def main():
         print("warning: fewer than 3 warm-up steps; the number is not a valid bench value", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.measure_peaks:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2605_25863_gb300 import linac
+        r = linac.linac_measure_int_rates()
+        r["imad_per_sm_per_clk"] = r["imad_wide_per_s"] / (r["sm_count"] * r["sm_clock_khz"] * 1e3)
+        r["device"] = torch.cuda.get_device_name(0)
+        print(json.dumps(r))
+        return 0
     return run_ours(args)
 
 

@@ -165,7 +165,15 @@ linac_status linac_solve_ex(const uint32_t *d_A, int64_t m, int64_t nA, int64_t 
  *                 0 ok; with LINAC_SHARED_PATTERN, bit 8 (0x100) marks a
  *                 system that needed the full pivot search.
  *   max_m, max_n  upper bounds of d_m and d_n (host values, used to size the
- *                 launch); systems with n > 1024 or m > 65535 are rejected.
+ *                 launches); m > 1024 or n > 1024 is rejected.
+ * Systems are counting-sorted by row count on the device and reduced one per
+ * thread block, largest first, in per-size-bucket persistent launches whose
+ * panel widths come from linac_batched_tune (or defaults).  With
+ * LINAC_SHARED_PATTERN, system 0 is the probe: its pivot rows and columns are
+ * reused for every system of the same shape, and a system whose reused pivot
+ * vanishes (or whose result leaves echelon form) is reduced again with the
+ * search, starting from its partially reduced rows (row operations preserve
+ * the RREF).
  * Errors: as linac_rref; LINAC_ERR_UNSUPPORTED for sizes above the limits.
  */
 linac_status linac_rref_batched(uint32_t *d_data, const int64_t *d_offsets,
@@ -202,6 +210,21 @@ void linac_profile_enable(int on);
 void linac_profile_reset(void);
 int linac_profile_read(linac_profile_entry *out, int max_entries);
 long long linac_launch_count(void);
+
+/* Throughput of the integer pipes the two trailing-update paths run on,
+ * measured by short saturating probes on the current device (allocates a
+ * small buffer; synchronises `stream`): thread-level mad.wide.u32 per second
+ * (plain path), u8 multiply-adds per second of mma.sync m16n8k32 (limb path)
+ * and of dp4a.  Diagnostic only; the paper has no counterpart. */
+typedef struct {
+    double imad_wide_per_s;
+    double imma_u8_mac_per_s;
+    double dp4a_u8_mac_per_s;
+    double sm_clock_khz;      /* nominal maximum SM clock */
+    int sm_count;
+} linac_int_rates;
+
+linac_status linac_measure_int_rates(linac_int_rates *out, cudaStream_t stream);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t linac_version(void);

@@ -250,7 +250,7 @@ linac_status linac_rref_batched(uint32_t* d_data, const int64_t* d_offsets, cons
         return LINAC_ERR_ARG;
     if ((uintptr_t)d_data % 16) return LINAC_ERR_ALIGN;
     if (flags & ~LINAC_SHARED_PATTERN) return LINAC_ERR_ARG;
-    if (max_n > 1024 || max_m > 65535) return LINAC_ERR_UNSUPPORTED;
+    if (max_n > 1024 || max_m > 1024) return LINAC_ERR_UNSUPPORTED;
     if (!prime_ok(p)) return LINAC_ERR_PRIME;
     const Field f = make_field(p);
     linac_status s = reset_status(stream);

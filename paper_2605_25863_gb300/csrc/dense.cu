@@ -196,17 +196,24 @@ gather_f_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, i
     }
 }
 
-// W[t][j] = M[Pi_t][c0 + j], j < n - c0.
-__global__ void gather_w_kernel(const uint32_t* __restrict__ M, int64_t ld, int64_t ncols, int c0,
-                                const DenseState* __restrict__ st, uint32_t* __restrict__ W,
-                                int64_t ldW) {
+// W[t][j] = balanced(M[Pi_t][c0 + j]) for t < k, zero for t in [k, kpad); j < n - c0.
+__global__ void gather_w_kernel(const uint32_t* __restrict__ M, int64_t ld, int64_t ncols, int c0, Field f,
+                                const DenseState* __restrict__ st, int32_t* __restrict__ W, int64_t ldW) {
     const int t = blockIdx.y;
-    if (t >= st->k) return;
+    const int k = st->k;
+    const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
+    if (t >= kpad) return;
+    int32_t* dst = W + (int64_t)t * ldW;
+    if (t >= k) {
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ncols;
+             j += (int64_t)gridDim.x * blockDim.x)
+            dst[j] = 0;
+        return;
+    }
     const uint32_t* src = M + (int64_t)st->Pi[t] * ld + c0;
-    uint32_t* dst = W + (int64_t)t * ldW;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ncols;
          j += (int64_t)gridDim.x * blockDim.x)
-        dst[j] = src[j];
+        dst[j] = to_balanced(src[j], f);
 }
 
 // ---------------------------------------------------------------------------
@@ -223,27 +230,28 @@ __global__ void heads_inverse_kernel(DenseState* st, const uint32_t* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// 4. TRSM-style reduction of the pivot rows, one column tile per block.
-//
-// V = W[:, tile].  Forward: for s = 0..k-2 and every t > s with multiplier
-// f_ts = panelU[t][J_s] != 0: V_t <- h_s V_t - f_ts V_s (the panel's own
-// recurrence, now on full rows).  Scale: V_t <- V_t / h_t.  Backward: for
-// s = k-1..1 and t < s: V_t <- V_t - c_ts V_s with c_ts = panelU[t][J_s] / h_t,
-// which is V_t's entry at J_s after the forward pass and the scaling.
-__global__ void __launch_bounds__(256)
-trsm_kernel(const uint32_t* __restrict__ W, int64_t ldW, int64_t ncols, int c0, Field f,
-            const DenseState* __restrict__ st, const uint32_t* __restrict__ panelU,
-            int32_t* __restrict__ R, int64_t ldR) {
+// 4. TRSM-style reduction of the pivot rows.  The panel left the pivot rows
+// related to the original rows W = M[Pi, c0:n] by a fixed k x k transform:
+// forward, for s = 0..k-2 and every t > s whose multiplier f_ts = panelU[t][J_s]
+// is nonzero, V_t <- h_s V_t - f_ts V_s (the panel's own fraction-free
+// recurrence); scaling V_t <- V_t / h_t; backward, for s = k-1..1 and t < s,
+// V_t <- V_t - c_ts V_s with c_ts = panelU[t][J_s] / h_t (V_t's entry at J_s
+// after the forward pass and the scaling).  The composite is E = G^{-1}, with
+// G = M[Pi, J].  One block applies it to the k x k identity and stores E
+// transposed and balanced; the reduced pivot rows are then R = E W, a small
+// product on the same lazy-accumulation kernel as the trailing update.
+__global__ void __launch_bounds__(1024)
+einv_kernel(const DenseState* __restrict__ st, const uint32_t* __restrict__ panelU, int c0, Field f,
+            int32_t* __restrict__ Et) {
     extern __shared__ __align__(16) uint32_t sm[];
+    constexpr int S = NB_MAX + 1;
+    uint32_t* E = sm;                 // E[t][j], row stride S
+    uint32_t* Co = sm + NB_MAX * S;   // Co[t][s] = panelU[t][J_s]
     __shared__ uint32_t hs[NB_MAX], hinv[NB_MAX];
     __shared__ int Jl[NB_MAX];
     const int k = st->k;
     if (k == 0) return;
     const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
-    constexpr int TB = TRSM_TB;
-    uint32_t* V = sm;                         // NB_MAX x TB
-    uint32_t* Co = V + NB_MAX * TB;           // k x k coefficients, row stride NB_MAX
-    const int64_t j0 = (int64_t)blockIdx.x * TB;
     const int tid = threadIdx.x;
     for (int t = tid; t < k; t += blockDim.x) {
         Jl[t] = st->J[t] - c0;
@@ -252,37 +260,38 @@ trsm_kernel(const uint32_t* __restrict__ W, int64_t ldW, int64_t ncols, int c0, 
     __syncthreads();
     for (int t = tid; t < k; t += blockDim.x) hs[t] = panelU[(size_t)t * NB_MAX + Jl[t]];
     for (int e = tid; e < k * k; e += blockDim.x) {
-        const int t = e / k, s = e % k;
-        const uint32_t v = panelU[(size_t)t * NB_MAX + Jl[s]];
-        Co[t * NB_MAX + s] = s > t ? mulmod(v, hinv[t], f) : v;
-    }
-    for (int e = tid; e < k * TB; e += blockDim.x) {
-        const int t = e / TB, j = e % TB;
-        V[t * TB + j] = (j0 + j < ncols) ? W[(int64_t)t * ldW + j0 + j] : 0u;
+        const int t = e / k, j = e % k;
+        Co[t * S + j] = panelU[(size_t)t * NB_MAX + Jl[j]];
+        E[t * S + j] = t == j ? 1u : 0u;
     }
     __syncthreads();
     for (int s = 0; s + 1 < k; ++s) {
         const uint32_t h = hs[s];
-        for (int e = tid; e < (k - 1 - s) * TB; e += blockDim.x) {
-            const int t = s + 1 + e / TB, j = e % TB;
-            const uint32_t fts = Co[t * NB_MAX + s];
-            if (fts) V[t * TB + j] = mul2add(h, V[t * TB + j], f.p - fts, V[s * TB + j], f);
+        // rows t > s; E is lower triangular during this pass, so columns j <= t
+        for (int e = tid; e < (k - 1 - s) * k; e += blockDim.x) {
+            const int t = s + 1 + e / k, j = e % k;
+            const uint32_t fts = Co[t * S + s];
+            if (fts && j <= t) E[t * S + j] = mul2add(h, E[t * S + j], f.p - fts, E[s * S + j], f);
         }
         __syncthreads();
     }
-    for (int e = tid; e < k * TB; e += blockDim.x) V[e] = mulmod(V[e], hinv[e / TB], f);
+    for (int e = tid; e < k * k; e += blockDim.x) {
+        const int t = e / k, j = e % k;
+        E[t * S + j] = mulmod(E[t * S + j], hinv[t], f);
+    }
     __syncthreads();
     for (int s = k - 1; s >= 1; --s) {
-        for (int e = tid; e < s * TB; e += blockDim.x) {
-            const int t = e / TB, j = e % TB;
-            const uint32_t c = Co[t * NB_MAX + s];
-            if (c) V[t * TB + j] = mul2add(1u, V[t * TB + j], f.p - c, V[s * TB + j], f);
+        for (int e = tid; e < s * k; e += blockDim.x) {
+            const int t = e / k, j = e % k;
+            const uint32_t c = mulmod(Co[t * S + s], hinv[t], f);
+            if (c) E[t * S + j] = mul2add(1u, E[t * S + j], f.p - c, E[s * S + j], f);
         }
         __syncthreads();
     }
-    for (int e = tid; e < kpad * TB; e += blockDim.x) {
-        const int t = e / TB, j = e % TB;
-        if (j0 + j < ncols) R[(int64_t)t * ldR + j0 + j] = t < k ? to_balanced(V[t * TB + j], f) : 0;
+    // Et[s][t] = balanced E[t][s]; zero outside k x k (K rows up to kpad, all NB_MAX columns)
+    for (int e = tid; e < kpad * NB_MAX; e += blockDim.x) {
+        const int s = e / NB_MAX, t = e % NB_MAX;
+        Et[e] = (s < k && t < k) ? to_balanced(E[t * S + s], f) : 0;
     }
 }
 
@@ -384,7 +393,7 @@ __global__ void validate_kernel(const uint32_t* __restrict__ A, int64_t m, int64
 namespace {
 
 struct DenseLayout {
-    size_t off_state, off_cand, off_panel, off_ft, off_w, off_r, total;
+    size_t off_state, off_cand, off_panel, off_e, off_ft, off_w, off_r, total;
     int64_t ldF, ldW;
 };
 
@@ -394,6 +403,7 @@ DenseLayout dense_layout(int64_t m, int64_t n, int G) {
     L.off_state = o; o = align_up(o + sizeof(DenseState), 256);
     L.off_cand = o;  o = align_up(o + (size_t)2 * G * NB_MAX * 4, 256);
     L.off_panel = o; o = align_up(o + (size_t)NB_MAX * NB_MAX * 4, 256);
+    L.off_e = o;     o = align_up(o + (size_t)NB_MAX * NB_MAX * 4, 256);
     L.ldF = (int64_t)align_up((size_t)std::max<int64_t>(m, 1), 4);
     L.off_ft = o;    o = align_up(o + (size_t)NB_MAX * L.ldF * 4, 256);
     L.ldW = (int64_t)align_up((size_t)std::max<int64_t>(n, 1), 4);
@@ -455,14 +465,14 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
     uint32_t* cand = (uint32_t*)(ws + L.off_cand);
     uint32_t* panelU = (uint32_t*)(ws + L.off_panel);
     int32_t* Ft = (int32_t*)(ws + L.off_ft);
-    uint32_t* W = (uint32_t*)(ws + L.off_w);
+    int32_t* Et = (int32_t*)(ws + L.off_e);
+    int32_t* W = (int32_t*)(ws + L.off_w);
     int32_t* R = (int32_t*)(ws + L.off_r);
 
     LINAC_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)psmem));
-    const size_t tsmem = (size_t)(NB_MAX * TRSM_TB + NB_MAX * NB_MAX) * 4;
-    LINAC_CUDA_TRY(cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)tsmem));
+    LINAC_CUDA_TRY(cudaFuncSetAttribute(einv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)EINV_SMEM));
     int occ = 0;
     LINAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_kernel, PANEL_THREADS, psmem));
     if (occ < 1 || G > occ * sm_count()) return LINAC_ERR_UNSUPPORTED;
@@ -508,7 +518,8 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
         {
             const unsigned gx = (unsigned)std::min<int64_t>((ncols + 1023) / 1024, 64);
             ProfScope ps(stream, PROF_GATHER_W);
-            gather_w_kernel<<<dim3(std::max(1u, gx), NB_MAX), 256, 0, stream>>>(dA, ld, ncols, (int)c0, st, W, L.ldW);
+            gather_w_kernel<<<dim3(std::max(1u, gx), NB_MAX), 256, 0, stream>>>(dA, ld, ncols, (int)c0, f, st, W,
+                                                                                 L.ldW);
         }
         {
             ProfScope ps(stream, PROF_INVERSE);
@@ -516,8 +527,11 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
         }
         {
             ProfScope ps(stream, PROF_TRSM);
-            trsm_kernel<<<(unsigned)((ncols + TRSM_TB - 1) / TRSM_TB), 256, tsmem, stream>>>(
-                W, L.ldW, ncols, (int)c0, f, st, panelU, R, L.ldW);
+            einv_kernel<<<1, 1024, EINV_SMEM, stream>>>(st, panelU, (int)c0, f, Et);
+        }
+        {
+            linac_status gs = launch_gemm_assign(f, st, Et, NB_MAX, W, L.ldW, ncols, R, L.ldW, stream);
+            if (gs != LINAC_OK) return gs;
         }
         {
             ProfScope ps(stream, PROF_MOVE);

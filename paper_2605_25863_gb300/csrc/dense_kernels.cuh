@@ -8,7 +8,7 @@
 namespace linac {
 
 constexpr int PANEL_THREADS = 256;   // block size of panel_kernel
-constexpr int TRSM_TB = 64;          // columns per trsm_kernel block
+constexpr size_t EINV_SMEM = (size_t)2 * NB_MAX * (NB_MAX + 1) * 4;   // einv_kernel dynamic smem
 
 __global__ void init_kernel(DenseState* st, int32_t* d_pivots, int64_t npiv, int32_t* d_rank);
 __global__ void finish_kernel(DenseState* st, int32_t* d_pivots, int32_t* d_rank);
@@ -18,15 +18,13 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
 __global__ void __launch_bounds__(256)
 gather_f_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f,
                 const DenseState* __restrict__ st, int32_t* __restrict__ Ft, int64_t ldF);
-__global__ void gather_w_kernel(const uint32_t* __restrict__ M, int64_t ld, int64_t ncols, int c0,
-                                const DenseState* __restrict__ st, uint32_t* __restrict__ W,
-                                int64_t ldW);
+__global__ void gather_w_kernel(const uint32_t* __restrict__ M, int64_t ld, int64_t ncols, int c0, Field f,
+                                const DenseState* __restrict__ st, int32_t* __restrict__ W, int64_t ldW);
 __global__ void heads_inverse_kernel(DenseState* st, const uint32_t* __restrict__ panelU, int c0,
                                      uint32_t p, int* status);
-__global__ void __launch_bounds__(256)
-trsm_kernel(const uint32_t* __restrict__ W, int64_t ldW, int64_t ncols, int c0, Field f,
-            const DenseState* __restrict__ st, const uint32_t* __restrict__ panelU,
-            int32_t* __restrict__ R, int64_t ldR);
+__global__ void __launch_bounds__(1024)
+einv_kernel(const DenseState* __restrict__ st, const uint32_t* __restrict__ panelU, int c0, Field f,
+            int32_t* __restrict__ Et);
 __global__ void __launch_bounds__(256)
 move_kernel(uint32_t* __restrict__ M, int64_t ld, int64_t n, int c0, const DenseState* __restrict__ st,
             int32_t* __restrict__ Ft, int64_t ldF);

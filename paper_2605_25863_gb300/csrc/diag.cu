@@ -1,0 +1,104 @@
+// diag.cu -- throughput probes for the roofline denominators of the two
+// trailing-update paths: the 32-bit integer multiply-add pipe (mad.wide.u32,
+// the instruction of the plain path) and the integer tensor pipe
+// (mma.sync m16n8k32 u8 -> s32, the instruction of the limb path), plus dp4a
+// for comparison.  Each probe keeps many independent chains in flight so the
+// pipe, not latency, is the limit.
+#include <cuda_runtime.h>
+
+#include "../../include/linac.h"
+#include "linac_host.h"
+
+namespace linac {
+
+__global__ void probe_imad_wide(unsigned long long* out, uint32_t seed, int iters) {
+    uint32_t a[8];
+    unsigned long long acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) { a[j] = seed * (j + 1) + threadIdx.x; acc[j] = j; }
+    const uint32_t b = seed ^ 0x9e3779b9u;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[j]) : "r"(a[j]), "r"(b));
+    }
+    unsigned long long s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) s += acc[j];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void probe_dp4a(int* out, uint32_t seed, int iters) {
+    int a[8], acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) { a[j] = (int)(seed * (j + 1) + threadIdx.x); acc[j] = j; }
+    const int b = (int)(seed ^ 0x9e3779b9u);
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) asm volatile("dp4a.u32.u32 %0, %1, %2, %0;" : "+r"(acc[j]) : "r"(a[j]), "r"(b));
+    }
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) s += acc[j];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void probe_imma_u8(int* out, uint32_t seed, int iters) {
+    const uint32_t a0 = seed ^ threadIdx.x, a1 = a0 * 3, a2 = a0 * 5, a3 = a0 * 7, b0 = a0 * 11, b1 = a0 * 13;
+    int d[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) d[c][0] = d[c][1] = d[c][2] = d[c][3] = 0;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            asm volatile(
+                "mma.sync.aligned.m16n8k32.row.col.s32.u8.u8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+r"(d[c][0]), "+r"(d[c][1]), "+r"(d[c][2]), "+r"(d[c][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+    int s = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) s += d[c][0] + d[c][1] + d[c][2] + d[c][3];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace linac
+
+using namespace linac;
+
+extern "C" linac_status linac_measure_int_rates(linac_int_rates* out, cudaStream_t stream) {
+    if (!out) return LINAC_ERR_ARG;
+    const int nsm = sm_count();
+    const int grid = nsm * 8, threads = 256, iters = 4096;
+    void* buf = nullptr;
+    LINAC_CUDA_TRY(cudaMalloc(&buf, (size_t)grid * threads * 8));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float ms = 0.f;
+    auto time_it = [&](auto launch) -> double {
+        launch(16);   // warm-up
+        cudaEventRecord(e0, stream);
+        launch(iters);
+        cudaEventRecord(e1, stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms * 1e-3;
+    };
+    const double lanes = (double)grid * threads;
+    double t = time_it([&](int it) { probe_imad_wide<<<grid, threads, 0, stream>>>((unsigned long long*)buf, 1u, it); });
+    out->imad_wide_per_s = lanes * iters * 8 / t;
+    t = time_it([&](int it) { probe_dp4a<<<grid, threads, 0, stream>>>((int*)buf, 1u, it); });
+    out->dp4a_u8_mac_per_s = lanes * iters * 8 * 4 / t;
+    t = time_it([&](int it) { probe_imma_u8<<<grid, threads, 0, stream>>>((int*)buf, 1u, it); });
+    out->imma_u8_mac_per_s = (double)grid * (threads / 32) * iters * 4 * 4096.0 / t;
+    int clk = 0;
+    cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
+    out->sm_clock_khz = clk;
+    out->sm_count = nsm;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaGetLastError();
+    cudaFree(buf);
+    return e == cudaSuccess ? LINAC_OK : LINAC_ERR_CUDA;
+}

@@ -76,6 +76,28 @@ __device__ __forceinline__ int64_t fold64(int64_t acc, const Field& f) {
     return (int64_t)H * (int64_t)f.c32 + (int64_t)L;
 }
 
+// acc += a * b as one fused signed 32 x 32 -> 64 multiply-add (the
+// accumulator is the 64-bit addend of mad.wide.s32).
+__device__ __forceinline__ void mac_s64(int64_t& acc, int32_t a, int32_t b) {
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+// fold64 as a two-instruction carry chain: low word lo(H*c32) + L with carry
+// out, high word hi(H*c32) (signed; c32 < 2^31) plus the carry.
+__device__ __forceinline__ int64_t fold64_fast(int64_t acc, const Field& f) {
+    int64_t out;
+    asm("{\n\t"
+        ".reg .u32 lo, hi, rlo, rhi;\n\t"
+        "mov.b64 {lo, hi}, %1;\n\t"
+        "mad.lo.cc.u32 rlo, hi, %2, lo;\n\t"
+        "madc.hi.s32 rhi, hi, %2, 0;\n\t"
+        "mov.b64 %0, {rlo, rhi};\n\t"
+        "}"
+        : "=l"(out)
+        : "l"(acc), "r"(f.c32));
+    return out;
+}
+
 // Canonical residue of a signed 64-bit accumulator with |acc| < 2^63.
 __device__ __forceinline__ uint32_t reduce_signed(int64_t acc, const Field& f) {
     int64_t t = fold64(acc, f);            // |t| < 2^31 * c32 + 2^32 <= 2^31 * p + 2^32

@@ -45,7 +45,7 @@ constexpr int kNoallocMaxGrid = (int)((kNoallocMaxDim + 127) / 128);   // panel 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 struct NoallocLayout {
-    size_t off_status, off_state, off_cand, off_panel, off_ft, off_w, off_r, total;
+    size_t off_status, off_state, off_cand, off_panel, off_e, off_ft, off_w, off_r, total;
     int64_t ldF, ldW;
 };
 
@@ -56,6 +56,7 @@ NoallocLayout noalloc_layout(int64_t m, int64_t n) {
     L.off_state = o;  o = align_up(o + sizeof(DenseState), 256);
     L.off_cand = o;   o = align_up(o + (size_t)2 * kNoallocMaxGrid * NB_MAX * 4, 256);
     L.off_panel = o;  o = align_up(o + (size_t)NB_MAX * NB_MAX * 4, 256);
+    L.off_e = o;      o = align_up(o + (size_t)NB_MAX * NB_MAX * 4, 256);
     L.ldF = (int64_t)align_up((size_t)std::max<int64_t>(m, 1), 4);
     L.off_ft = o;     o = align_up(o + (size_t)NB_MAX * L.ldF * 4, 256);
     L.ldW = (int64_t)align_up((size_t)std::max<int64_t>(n, 1), 4);
@@ -121,12 +122,12 @@ extern "C" linac_status linac_rref_noalloc(uint32_t* d_A, int64_t m, int64_t n, 
     uint32_t* cand = (uint32_t*)(ws + L.off_cand);
     uint32_t* panelU = (uint32_t*)(ws + L.off_panel);
     int32_t* Ft = (int32_t*)(ws + L.off_ft);
-    uint32_t* W = (uint32_t*)(ws + L.off_w);
+    int32_t* Et = (int32_t*)(ws + L.off_e);
+    int32_t* W = (int32_t*)(ws + L.off_w);
     int32_t* R = (int32_t*)(ws + L.off_r);
 
     LINAC_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
-    const size_t tsmem = (size_t)(NB_MAX * TRSM_TB + NB_MAX * NB_MAX) * 4;
-    LINAC_CUDA_TRY(cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+    LINAC_CUDA_TRY(cudaFuncSetAttribute(einv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EINV_SMEM));
     int occ = 0;
     LINAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_kernel, PANEL_THREADS, psmem));
     if (occ < 1 || G > occ * sm_count()) return LINAC_ERR_UNSUPPORTED;
@@ -154,10 +155,11 @@ extern "C" linac_status linac_rref_noalloc(uint32_t* d_A, int64_t m, int64_t n, 
         }
         gather_f_kernel<<<(unsigned)((m + 63) / 64), 256, 0, stream>>>(d_A, m, ld, (int)c0, w, f, st, Ft, L.ldF);
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncols + 1023) / 1024, 64));
-        gather_w_kernel<<<dim3(gx, NB_MAX), 256, 0, stream>>>(d_A, ld, ncols, (int)c0, st, W, L.ldW);
+        gather_w_kernel<<<dim3(gx, NB_MAX), 256, 0, stream>>>(d_A, ld, ncols, (int)c0, f, st, W, L.ldW);
         heads_inverse_kernel<<<1, NB_MAX, 0, stream>>>(st, panelU, (int)c0, f.p, status);
-        trsm_kernel<<<(unsigned)((ncols + TRSM_TB - 1) / TRSM_TB), 256, tsmem, stream>>>(
-            W, L.ldW, ncols, (int)c0, f, st, panelU, R, L.ldW);
+        einv_kernel<<<1, 1024, EINV_SMEM, stream>>>(st, panelU, (int)c0, f, Et);
+        s = launch_gemm_assign(f, st, Et, NB_MAX, W, L.ldW, ncols, R, L.ldW, stream);
+        if (s != LINAC_OK) return s;
         move_kernel<<<NB_MAX, 256, 0, stream>>>(d_A, ld, n, (int)c0, st, Ft, L.ldF);
         s = launch_update(LINAC_PATH_PLAIN, d_A, m, n, ld, (int)c0, f, st, Ft, L.ldF, R, L.ldW, nullptr, stream);
         if (s != LINAC_OK) return s;

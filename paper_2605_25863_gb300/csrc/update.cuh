@@ -40,6 +40,12 @@ linac_status launch_update(int path, uint32_t* M, int64_t m, int64_t n, int64_t 
                            const int32_t* R, int64_t ldR, const LimbScratch* limb,
                            cudaStream_t stream);
 
+// R[t][j] <- balanced(sum_s E[t][s] W[s][j]) for t < kpad(k), j < ncols, with
+// Et = E transposed (kpad x ldE) and W (kpad x ldW), both balanced int32.
+linac_status launch_gemm_assign(const Field& f, const DenseState* st, const int32_t* Et, int64_t ldE,
+                                const int32_t* W, int64_t ldW, int64_t ncols, int32_t* R, int64_t ldR,
+                                cudaStream_t stream);
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)

@@ -21,11 +21,14 @@
 
 namespace linac {
 
-template <int FOLD>
+// MODE 0: trailing update of M (rows [r, r+k) receive R).  MODE 1: plain
+// product written as balanced residues to Out (k_pad x ldOut); M, m, c0 unused
+// except that m bounds the A rows read.
+template <int FOLD, int MODE>
 __global__ void __launch_bounds__(256, 1)
 update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, int c0, Field f,
                     const DenseState* __restrict__ st, const int32_t* __restrict__ Ft, int64_t ldF,
-                    const int32_t* __restrict__ R, int64_t ldR) {
+                    const int32_t* __restrict__ R, int64_t ldR, int32_t* __restrict__ Out, int64_t ldOut) {
     static_assert(UPD_BK % FOLD == 0, "fold cadence must divide the K chunk");
     __shared__ __align__(16) int32_t As[2][UPD_BK][UPD_BM];
     __shared__ __align__(16) int32_t Bs[2][UPD_BK][UPD_BN];
@@ -87,17 +90,33 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] += (int64_t)a[i] * (int64_t)b[j];
+                for (int j = 0; j < 8; ++j) mac_s64(acc[i][j], a[i], b[j]);
             if ((kk + 1) % FOLD == 0) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fold64(acc[i][j], f);
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fold64_fast(acc[i][j], f);
             }
         }
         __syncthreads();
     }
 
+    if (MODE == 1) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t row = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+            if (row >= kpad) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t col = col0 + h * 64 + tx * 4;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (col + q < ncols)
+                        Out[row * ldOut + col + q] = to_balanced(reduce_signed(acc[i][h * 4 + q], f), f);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int64_t row = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
@@ -147,11 +166,28 @@ linac_status launch_update(int path, uint32_t* M, int64_t m, int64_t n, int64_t 
     dim3 grid((unsigned)((ncols + UPD_BN - 1) / UPD_BN), (unsigned)((m + UPD_BM - 1) / UPD_BM));
     ProfScope ps(stream, PROF_UPDATE_PLAIN);
     if (f.fold >= 16)
-        update_plain_kernel<16><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR);
+        update_plain_kernel<16, 0><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, nullptr, 0);
     else if (f.fold >= 8)
-        update_plain_kernel<8><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR);
+        update_plain_kernel<8, 0><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, nullptr, 0);
     else
-        update_plain_kernel<4><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR);
+        update_plain_kernel<4, 0><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, nullptr, 0);
+    LINAC_CUDA_TRY(cudaGetLastError());
+    return LINAC_OK;
+}
+
+linac_status launch_gemm_assign(const Field& f, const DenseState* st, const int32_t* Et, int64_t ldE,
+                                const int32_t* W, int64_t ldW, int64_t ncols, int32_t* R, int64_t ldR,
+                                cudaStream_t stream) {
+    if (ncols <= 0) return LINAC_OK;
+    dim3 grid((unsigned)((ncols + UPD_BN - 1) / UPD_BN), 1);
+    ProfScope ps(stream, PROF_TRSM);
+    // A rows are the NB_MAX columns of Et (zero beyond k); K runs to kpad(k)
+    if (f.fold >= 8)
+        update_plain_kernel<8, 1><<<grid, 256, 0, stream>>>(nullptr, NB_MAX, ncols, 0, 0, f, st, Et, ldE, W, ldW,
+                                                           R, ldR);
+    else
+        update_plain_kernel<4, 1><<<grid, 256, 0, stream>>>(nullptr, NB_MAX, ncols, 0, 0, f, st, Et, ldE, W, ldW,
+                                                           R, ldR);
     LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;
 }

@@ -37,6 +37,12 @@ class Options(ctypes.Structure):
                 ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class IntRates(ctypes.Structure):
+    _fields_ = [("imad_wide_per_s", ctypes.c_double), ("imma_u8_mac_per_s", ctypes.c_double),
+                ("dp4a_u8_mac_per_s", ctypes.c_double), ("sm_clock_khz", ctypes.c_double),
+                ("sm_count", ctypes.c_int)]
+
+
 class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
 
@@ -76,6 +82,8 @@ def lib():
         L.linac_profile_reset.restype = None
         L.linac_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), ctypes.c_int]
         L.linac_profile_read.restype = ctypes.c_int
+        L.linac_measure_int_rates.argtypes = [ctypes.POINTER(IntRates), vp]
+        L.linac_measure_int_rates.restype = ctypes.c_int
         L.linac_launch_count.argtypes = []
         L.linac_launch_count.restype = ctypes.c_longlong
         for name in ("linac_rref", "linac_rref_ex", "linac_solve", "linac_solve_ex",
@@ -226,3 +234,10 @@ def linac_profile_read() -> dict:
 
 def linac_launch_count() -> int:
     return int(lib().linac_launch_count())
+
+
+def linac_measure_int_rates(stream=None) -> dict:
+    """Measured integer pipe rates of the current device (see include/linac.h)."""
+    r = IntRates()
+    _check(lib().linac_measure_int_rates(ctypes.byref(r), _stream_ptr(stream)), "linac_measure_int_rates")
+    return {k: getattr(r, k) for k, _ in IntRates._fields_}

@@ -48,7 +48,7 @@ def test_uniform_vs_oracle(shape, p):
 
 
 @pytest.mark.parametrize("nb", [16, 32, 64, 128])
-@pytest.mark.parametrize("path", ["plain", "auto"])
+@pytest.mark.parametrize("path", ["plain", "auto", "limb"])
 def test_panel_widths(nb, path):
     M, _ = synth.rank_deficient(m=333, n=401, d=21, p=P31, seed=nb)
     check_against_oracle(M, P31, nb=nb, path=path)
@@ -169,3 +169,25 @@ def test_repeated_calls_reuse_scratch_and_match():
     R1, r1, p1 = gpu_rref(M, P31)
     R2, r2, p2 = gpu_rref(M, P31)
     assert r1 == r2 and np.array_equal(R1, R2) and np.array_equal(p1, p2)
+
+
+@pytest.mark.parametrize("p", [3, 251, 65537, P31, PB])
+@pytest.mark.parametrize("shape", [(37, 45), (300, 300), (513, 700), (1000, 1100)])
+def test_limb_path_vs_oracle(shape, p):
+    """The u8-limb integer-tensor update gives the same RREF as the oracle."""
+    m, n = shape
+    M = synth.uniform(shape, p, synth.stream_key(m * 31 + n, f"limb{p}"))
+    check_against_oracle(M, p, path="limb")
+
+
+@pytest.mark.parametrize("nb", [16, 32, 64, 128])
+def test_limb_path_rank_deficient(nb):
+    M, _ = synth.rank_deficient(m=700, n=650, d=33, p=PB, seed=nb + 100)
+    check_against_oracle(M, PB, path="limb", nb=nb)
+
+
+def test_limb_and_plain_agree_on_workload_4096():
+    M, _ = synth.rank_deficient()
+    Rl, rl, pl = gpu_rref(M, P31, path="limb")
+    Rp, rp, pp = gpu_rref(M, P31, path="plain")
+    assert rl == rp == 4032 and np.array_equal(pl, pp) and np.array_equal(Rl, Rp)
