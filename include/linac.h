@@ -213,7 +213,7 @@ long long linac_launch_count(void);
 
 /* Throughput of the integer pipes the two trailing-update paths run on,
  * measured by short saturating probes on the current device (allocates a
- * small buffer; synchronises `stream`): thread-level mad.wide.u32 per second
+ * small buffer; synchronises `stream`): thread-level mad.wide.s32 per second
  * (plain path), u8 multiply-adds per second of mma.sync m16n8k32 (limb path)
  * and of dp4a.  Diagnostic only; the paper has no counterpart. */
 typedef struct {

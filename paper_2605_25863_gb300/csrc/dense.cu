@@ -237,22 +237,30 @@ __global__ void heads_inverse_kernel(DenseState* st, const uint32_t* __restrict_
 // recurrence); scaling V_t <- V_t / h_t; backward, for s = k-1..1 and t < s,
 // V_t <- V_t - c_ts V_s with c_ts = panelU[t][J_s] / h_t (V_t's entry at J_s
 // after the forward pass and the scaling).  The composite is E = G^{-1}, with
-// G = M[Pi, J].  One block applies it to the k x k identity and stores E
-// transposed and balanced; the reduced pivot rows are then R = E W, a small
+// G = M[Pi, J].  Columns of E are independent (column j is the transform of
+// the unit vector e_j), so each block builds EINV_COLS columns; E is stored
+// transposed and balanced, and the reduced pivot rows are R = E W, a small
 // product on the same lazy-accumulation kernel as the trailing update.
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 einv_kernel(const DenseState* __restrict__ st, const uint32_t* __restrict__ panelU, int c0, Field f,
             int32_t* __restrict__ Et) {
     extern __shared__ __align__(16) uint32_t sm[];
     constexpr int S = NB_MAX + 1;
-    uint32_t* E = sm;                 // E[t][j], row stride S
-    uint32_t* Co = sm + NB_MAX * S;   // Co[t][s] = panelU[t][J_s]
+    constexpr int C = EINV_COLS;
+    uint32_t* Co = sm;                 // Co[t][s]: f_ts (s < t) or c_ts (s > t)
+    uint32_t* Ec = sm + NB_MAX * S;    // Ec[t][c] = E[t][j0 + c]
     __shared__ uint32_t hs[NB_MAX], hinv[NB_MAX];
     __shared__ int Jl[NB_MAX];
     const int k = st->k;
     if (k == 0) return;
     const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
+    const int j0 = blockIdx.x * C;
+    if (j0 >= kpad) return;
     const int tid = threadIdx.x;
+    if (j0 >= k) {   // padding rows of Et
+        for (int e = tid; e < C * NB_MAX; e += blockDim.x) Et[(size_t)(j0 + e / NB_MAX) * NB_MAX + e % NB_MAX] = 0;
+        return;
+    }
     for (int t = tid; t < k; t += blockDim.x) {
         Jl[t] = st->J[t] - c0;
         hinv[t] = st->hinv[t];
@@ -260,38 +268,41 @@ einv_kernel(const DenseState* __restrict__ st, const uint32_t* __restrict__ pane
     __syncthreads();
     for (int t = tid; t < k; t += blockDim.x) hs[t] = panelU[(size_t)t * NB_MAX + Jl[t]];
     for (int e = tid; e < k * k; e += blockDim.x) {
-        const int t = e / k, j = e % k;
-        Co[t * S + j] = panelU[(size_t)t * NB_MAX + Jl[j]];
-        E[t * S + j] = t == j ? 1u : 0u;
+        const int t = e / k, s = e % k;
+        const uint32_t v = panelU[(size_t)t * NB_MAX + Jl[s]];
+        Co[t * S + s] = s > t ? mulmod(v, hinv[t], f) : v;
+    }
+    for (int e = tid; e < k * C; e += blockDim.x) {
+        const int t = e / C, c = e % C;
+        Ec[t * C + c] = (t == j0 + c) ? 1u : 0u;
     }
     __syncthreads();
+    // forward (all stages: row j itself is rescaled by h_s at every earlier
+    // stage s whose multiplier f_js is nonzero, so E[j][j] changes before s = j)
     for (int s = 0; s + 1 < k; ++s) {
         const uint32_t h = hs[s];
-        // rows t > s; E is lower triangular during this pass, so columns j <= t
-        for (int e = tid; e < (k - 1 - s) * k; e += blockDim.x) {
-            const int t = s + 1 + e / k, j = e % k;
+        for (int e = tid; e < (k - 1 - s) * C; e += blockDim.x) {
+            const int t = s + 1 + e / C, c = e % C;
             const uint32_t fts = Co[t * S + s];
-            if (fts && j <= t) E[t * S + j] = mul2add(h, E[t * S + j], f.p - fts, E[s * S + j], f);
+            if (fts) Ec[t * C + c] = mul2add(h, Ec[t * C + c], f.p - fts, Ec[s * C + c], f);
         }
         __syncthreads();
     }
-    for (int e = tid; e < k * k; e += blockDim.x) {
-        const int t = e / k, j = e % k;
-        E[t * S + j] = mulmod(E[t * S + j], hinv[t], f);
-    }
+    for (int e = tid; e < k * C; e += blockDim.x) Ec[e] = mulmod(Ec[e], hinv[e / C], f);
     __syncthreads();
     for (int s = k - 1; s >= 1; --s) {
-        for (int e = tid; e < s * k; e += blockDim.x) {
-            const int t = e / k, j = e % k;
-            const uint32_t c = mulmod(Co[t * S + s], hinv[t], f);
-            if (c) E[t * S + j] = mul2add(1u, E[t * S + j], f.p - c, E[s * S + j], f);
+        for (int e = tid; e < s * C; e += blockDim.x) {
+            const int t = e / C, c = e % C;
+            const uint32_t cts = Co[t * S + s];
+            if (cts) Ec[t * C + c] = mul2add(1u, Ec[t * C + c], f.p - cts, Ec[s * C + c], f);
         }
         __syncthreads();
     }
-    // Et[s][t] = balanced E[t][s]; zero outside k x k (K rows up to kpad, all NB_MAX columns)
-    for (int e = tid; e < kpad * NB_MAX; e += blockDim.x) {
-        const int s = e / NB_MAX, t = e % NB_MAX;
-        Et[e] = (s < k && t < k) ? to_balanced(E[t * S + s], f) : 0;
+    // Et[j][t] = balanced E[t][j] for the block's columns j; zero for t >= k
+    for (int e = tid; e < C * NB_MAX; e += blockDim.x) {
+        const int c = e / NB_MAX, t = e % NB_MAX;
+        const int j = j0 + c;
+        Et[(size_t)j * NB_MAX + t] = (j < k && t < k) ? to_balanced(Ec[t * C + c], f) : 0;
     }
 }
 
@@ -527,7 +538,7 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
         }
         {
             ProfScope ps(stream, PROF_TRSM);
-            einv_kernel<<<1, 1024, EINV_SMEM, stream>>>(st, panelU, (int)c0, f, Et);
+            einv_kernel<<<NB_MAX / EINV_COLS, 256, EINV_SMEM, stream>>>(st, panelU, (int)c0, f, Et);
         }
         {
             linac_status gs = launch_gemm_assign(f, st, Et, NB_MAX, W, L.ldW, ncols, R, L.ldW, stream);

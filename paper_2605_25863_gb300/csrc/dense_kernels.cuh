@@ -8,7 +8,8 @@
 namespace linac {
 
 constexpr int PANEL_THREADS = 256;   // block size of panel_kernel
-constexpr size_t EINV_SMEM = (size_t)2 * NB_MAX * (NB_MAX + 1) * 4;   // einv_kernel dynamic smem
+constexpr int EINV_COLS = 8;         // columns of E = G^{-1} per einv_kernel block
+constexpr size_t EINV_SMEM = ((size_t)NB_MAX * (NB_MAX + 1) + (size_t)NB_MAX * EINV_COLS) * 4;
 
 __global__ void init_kernel(DenseState* st, int32_t* d_pivots, int64_t npiv, int32_t* d_rank);
 __global__ void finish_kernel(DenseState* st, int32_t* d_pivots, int32_t* d_rank);
@@ -22,7 +23,7 @@ __global__ void gather_w_kernel(const uint32_t* __restrict__ M, int64_t ld, int6
                                 const DenseState* __restrict__ st, int32_t* __restrict__ W, int64_t ldW);
 __global__ void heads_inverse_kernel(DenseState* st, const uint32_t* __restrict__ panelU, int c0,
                                      uint32_t p, int* status);
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 einv_kernel(const DenseState* __restrict__ st, const uint32_t* __restrict__ panelU, int c0, Field f,
             int32_t* __restrict__ Et);
 __global__ void __launch_bounds__(256)

@@ -1,9 +1,11 @@
 // diag.cu -- throughput probes for the roofline denominators of the two
-// trailing-update paths: the 32-bit integer multiply-add pipe (mad.wide.u32,
-// the instruction of the plain path) and the integer tensor pipe
+// trailing-update paths: the integer multiply-add pipe (mad.wide.s32, the
+// instruction of the plain path) and the integer tensor pipe
 // (mma.sync m16n8k32 u8 -> s32, the instruction of the limb path), plus dp4a
 // for comparison.  Each probe keeps many independent chains in flight so the
-// pipe, not latency, is the limit.
+// pipe, not latency, is the limit, and feeds every multiply an operand that
+// changes each iteration (a loop-invariant product could be hoisted by the
+// compiler, turning the probe into an add-throughput probe).
 #include <cuda_runtime.h>
 
 #include "../../include/linac.h"
@@ -12,29 +14,31 @@
 namespace linac {
 
 __global__ void probe_imad_wide(unsigned long long* out, uint32_t seed, int iters) {
-    uint32_t a[8];
-    unsigned long long acc[8];
+    long long acc[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) { a[j] = seed * (j + 1) + threadIdx.x; acc[j] = j; }
-    const uint32_t b = seed ^ 0x9e3779b9u;
+    for (int j = 0; j < 8; j++) acc[j] = (long long)(seed * (j + 1) + threadIdx.x);
+    const int b = (int)(seed ^ 0x9e3779b9u) | 1;
     for (int it = 0; it < iters; it++) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[j]) : "r"(a[j]), "r"(b));
+        for (int j = 0; j < 8; j++) {
+            const int a = (int)(unsigned)acc[j];   // low word of the accumulator: data dependent
+            asm volatile("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc[j]) : "r"(a), "r"(b));
+        }
     }
-    unsigned long long s = 0;
+    long long s = 0;
 #pragma unroll
     for (int j = 0; j < 8; j++) s += acc[j];
-    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = (unsigned long long)s;
 }
 
 __global__ void probe_dp4a(int* out, uint32_t seed, int iters) {
-    int a[8], acc[8];
+    int acc[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) { a[j] = (int)(seed * (j + 1) + threadIdx.x); acc[j] = j; }
+    for (int j = 0; j < 8; j++) acc[j] = (int)(seed * (j + 1) + threadIdx.x);
     const int b = (int)(seed ^ 0x9e3779b9u);
     for (int it = 0; it < iters; it++) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) asm volatile("dp4a.u32.u32 %0, %1, %2, %0;" : "+r"(acc[j]) : "r"(a[j]), "r"(b));
+        for (int j = 0; j < 8; j++) asm volatile("dp4a.u32.u32 %0, %0, %1, %0;" : "+r"(acc[j]) : "r"(b));
     }
     int s = 0;
 #pragma unroll

@@ -157,7 +157,7 @@ extern "C" linac_status linac_rref_noalloc(uint32_t* d_A, int64_t m, int64_t n, 
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncols + 1023) / 1024, 64));
         gather_w_kernel<<<dim3(gx, NB_MAX), 256, 0, stream>>>(d_A, ld, ncols, (int)c0, f, st, W, L.ldW);
         heads_inverse_kernel<<<1, NB_MAX, 0, stream>>>(st, panelU, (int)c0, f.p, status);
-        einv_kernel<<<1, 1024, EINV_SMEM, stream>>>(st, panelU, (int)c0, f, Et);
+        einv_kernel<<<NB_MAX / EINV_COLS, 256, EINV_SMEM, stream>>>(st, panelU, (int)c0, f, Et);
         s = launch_gemm_assign(f, st, Et, NB_MAX, W, L.ldW, ncols, R, L.ldW, stream);
         if (s != LINAC_OK) return s;
         move_kernel<<<NB_MAX, 256, 0, stream>>>(d_A, ld, n, (int)c0, st, Ft, L.ldF);

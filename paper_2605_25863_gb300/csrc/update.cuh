@@ -10,7 +10,8 @@ namespace linac {
 
 constexpr int NB_MAX = 128;   // widest panel
 constexpr int UPD_BM = 128;   // update tile rows
-constexpr int UPD_BN = 128;   // update tile columns
+constexpr int UPD_BN = 128;   // update tile columns (limb path)
+constexpr int UPD_BN2 = 64;   // update tile columns (plain path: two blocks per SM)
 constexpr int UPD_BK = 16;    // update K chunk; panel widths are multiples of it
 
 // Device-resident state of one dense elimination (lives in scratch memory).

@@ -21,23 +21,49 @@
 
 namespace linac {
 
+// Fold of a signed lazy accumulator.  SHIFTS = 0: H*c32 + L on the integer
+// multiply pipe (any p).  SHIFTS = 1..3: c32 = 2^32 mod p has SHIFTS set bits
+// (2^e0 + 2^e1 + 2^e2), and H*c32 is formed with shifts and adds on the ALU
+// pipe, leaving the multiply pipe to the products (2^31 - 1 gives c32 = 2,
+// 2^31 - 19 gives c32 = 38).
+struct FoldShifts {
+    uint32_t e[3];
+};
+
+template <int SHIFTS>
+__device__ __forceinline__ int64_t fold_any(int64_t acc, const Field& f, const FoldShifts& fs) {
+    if (SHIFTS == 0) return fold64_fast(acc, f);
+    const int64_t h = acc >> 32;                  // signed high word
+    int64_t r = (int64_t)(uint32_t)acc;           // low word
+#pragma unroll
+    for (int i = 0; i < SHIFTS; ++i) r += (int64_t)((uint64_t)h << fs.e[i]);   // h * 2^e, two's complement
+    return r;
+}
+
 // MODE 0: trailing update of M (rows [r, r+k) receive R).  MODE 1: plain
 // product written as balanced residues to Out (k_pad x ldOut); M, m, c0 unused
 // except that m bounds the A rows read.
-template <int FOLD, int MODE>
-__global__ void __launch_bounds__(256, 1)
+//
+// Tiling: 128 x 64 outputs per 256-thread block, 8 x 4 per thread (two 4-row
+// groups, one 4-column group), 128 registers so two blocks share an SM; K in
+// chunks of 16 staged by cp.async double buffering.  The products occupy the
+// integer multiply pipe (one mad.wide.s32 each, about four pipe cycles per
+// warp instruction on this GPU), which bounds the kernel.
+template <int FOLD, int SHIFTS, int MODE>
+__global__ void __launch_bounds__(256, 2)
 update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, int c0, Field f,
-                    const DenseState* __restrict__ st, const int32_t* __restrict__ Ft, int64_t ldF,
-                    const int32_t* __restrict__ R, int64_t ldR, int32_t* __restrict__ Out, int64_t ldOut) {
+                    FoldShifts fs, const DenseState* __restrict__ st, const int32_t* __restrict__ Ft,
+                    int64_t ldF, const int32_t* __restrict__ R, int64_t ldR, int32_t* __restrict__ Out,
+                    int64_t ldOut) {
     static_assert(UPD_BK % FOLD == 0, "fold cadence must divide the K chunk");
     __shared__ __align__(16) int32_t As[2][UPD_BK][UPD_BM];
-    __shared__ __align__(16) int32_t Bs[2][UPD_BK][UPD_BN];
+    __shared__ __align__(16) int32_t Bs[2][UPD_BK][UPD_BN2];
     const int k = st->k;
     if (k == 0) return;
     const int r = st->r;
     const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
     const int64_t row0 = (int64_t)blockIdx.y * UPD_BM;
-    const int64_t col0 = (int64_t)blockIdx.x * UPD_BN;   // relative to c0
+    const int64_t col0 = (int64_t)blockIdx.x * UPD_BN2;   // relative to c0
     const int64_t ncols = n - c0;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 
@@ -46,27 +72,26 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
         for (int it = 0; it < 2; ++it) {
             const int c = tid + it * 256;
             const int kk = c >> 5, x4 = (c & 31) * 4;
-            {
-                const int64_t row = row0 + x4;
-                const int bytes = row + 4 <= m ? 16 : (row < m ? (int)(m - row) * 4 : 0);
-                const int32_t* src = bytes ? Ft + (int64_t)(k0 + kk) * ldF + row : Ft;
-                cp_async16(&As[stage][kk][x4], src, bytes);
-            }
-            {
-                const int64_t col = col0 + x4;
-                const int bytes = col + 4 <= ncols ? 16 : (col < ncols ? (int)(ncols - col) * 4 : 0);
-                const int32_t* src = bytes ? R + (int64_t)(k0 + kk) * ldR + col : R;
-                cp_async16(&Bs[stage][kk][x4], src, bytes);
-            }
+            const int64_t row = row0 + x4;
+            const int bytes = row + 4 <= m ? 16 : (row < m ? (int)(m - row) * 4 : 0);
+            const int32_t* src = bytes ? Ft + (int64_t)(k0 + kk) * ldF + row : Ft;
+            cp_async16(&As[stage][kk][x4], src, bytes);
+        }
+        {
+            const int kk = tid >> 4, x4 = (tid & 15) * 4;
+            const int64_t col = col0 + x4;
+            const int bytes = col + 4 <= ncols ? 16 : (col < ncols ? (int)(ncols - col) * 4 : 0);
+            const int32_t* src = bytes ? R + (int64_t)(k0 + kk) * ldR + col : R;
+            cp_async16(&Bs[stage][kk][x4], src, bytes);
         }
         cp_async_commit();
     };
 
-    int64_t acc[8][8];
+    int64_t acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
 
     const int nk = kpad / UPD_BK;
     load(0, 0);
@@ -84,18 +109,17 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
             const int4 a0 = *reinterpret_cast<const int4*>(&As[s][kk][ty * 4]);
             const int4 a1 = *reinterpret_cast<const int4*>(&As[s][kk][64 + ty * 4]);
             const int4 b0 = *reinterpret_cast<const int4*>(&Bs[s][kk][tx * 4]);
-            const int4 b1 = *reinterpret_cast<const int4*>(&Bs[s][kk][64 + tx * 4]);
             const int a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const int b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const int b[4] = {b0.x, b0.y, b0.z, b0.w};
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) mac_s64(acc[i][j], a[i], b[j]);
+                for (int j = 0; j < 4; ++j) acc[i][j] += (int64_t)a[i] * (int64_t)b[j];
             if ((kk + 1) % FOLD == 0) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fold64_fast(acc[i][j], f);
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fold_any<SHIFTS>(acc[i][j], f, fs);
             }
         }
         __syncthreads();
@@ -106,14 +130,10 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
         for (int i = 0; i < 8; ++i) {
             const int64_t row = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
             if (row >= kpad) continue;
+            const int64_t col = col0 + tx * 4;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t col = col0 + h * 64 + tx * 4;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (col + q < ncols)
-                        Out[row * ldOut + col + q] = to_balanced(reduce_signed(acc[i][h * 4 + q], f), f);
-            }
+            for (int q = 0; q < 4; ++q)
+                if (col + q < ncols) Out[row * ldOut + col + q] = to_balanced(reduce_signed(acc[i][q], f), f);
         }
         return;
     }
@@ -122,34 +142,69 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
         const int64_t row = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
         if (row >= m) continue;
         const bool pivot_row = row >= r && row < r + k;
+        const int64_t col = col0 + tx * 4;
+        if (col >= ncols) continue;
+        uint32_t* dst = M + row * ld + c0 + col;
+        uint32_t out[4];
+        if (pivot_row) {
+            const int32_t* rr = R + (int64_t)(row - r) * ldR + col;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t col = col0 + h * 64 + tx * 4;
-            if (col >= ncols) continue;
-            uint32_t* dst = M + row * ld + c0 + col;
-            uint32_t out[4];
-            if (pivot_row) {
-                const int32_t* rr = R + (int64_t)(row - r) * ldR + col;
+            for (int q = 0; q < 4; ++q) out[q] = col + q < ncols ? from_balanced(rr[q], f) : 0u;
+        } else if (col + 4 <= ncols) {
+            const uint4 cv = *reinterpret_cast<const uint4*>(dst);
+            const uint32_t c4[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) out[q] = col + q < ncols ? from_balanced(rr[q], f) : 0u;
-            } else if (col + 4 <= ncols) {
-                const uint4 cv = *reinterpret_cast<const uint4*>(dst);
-                const uint32_t c4[4] = {cv.x, cv.y, cv.z, cv.w};
+            for (int q = 0; q < 4; ++q) out[q] = submod(c4[q], reduce_signed(acc[i][q], f), f);
+        } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) out[q] = submod(c4[q], reduce_signed(acc[i][h * 4 + q], f), f);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    out[q] = col + q < ncols ? submod(dst[q], reduce_signed(acc[i][h * 4 + q], f), f) : 0u;
-            }
-            if (col + 4 <= ncols) {
-                *reinterpret_cast<uint4*>(dst) = make_uint4(out[0], out[1], out[2], out[3]);
-            } else {
-                for (int q = 0; q < 4 && col + q < ncols; ++q) dst[q] = out[q];
-            }
+            for (int q = 0; q < 4; ++q)
+                out[q] = col + q < ncols ? submod(dst[q], reduce_signed(acc[i][q], f), f) : 0u;
+        }
+        if (col + 4 <= ncols) {
+            *reinterpret_cast<uint4*>(dst) = make_uint4(out[0], out[1], out[2], out[3]);
+        } else {
+            for (int q = 0; q < 4 && col + q < ncols; ++q) dst[q] = out[q];
         }
     }
 }
+
+namespace {
+// Set bits of c32 when there are at most three of them (0 = use the multiply fold).
+int fold_shifts(const Field& f, FoldShifts* fs) {
+    uint32_t c = f.c32;
+    int n = 0;
+    for (int b = 0; b < 32; ++b)
+        if ((c >> b) & 1u) {
+            if (n == 3) return 0;
+            fs->e[n++] = (uint32_t)b;
+        }
+    for (int i = n; i < 3; ++i) fs->e[i] = 0;
+    return n;
+}
+
+template <int MODE>
+void launch_plain(dim3 grid, cudaStream_t stream, uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0,
+                  const Field& f, const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,
+                  int64_t ldR, int32_t* Out, int64_t ldOut) {
+    FoldShifts fs;
+    const int sh = fold_shifts(f, &fs);
+    const int fold = f.fold >= 16 ? 16 : (f.fold >= 8 ? 8 : 4);
+#define LINAC_UPD(FO, SH) \
+    update_plain_kernel<FO, SH, MODE><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, fs, st, Ft, ldF, R, ldR, Out, ldOut)
+#define LINAC_UPD_SH(FO)                    \
+    switch (sh) {                           \
+        case 1: LINAC_UPD(FO, 1); break;    \
+        case 2: LINAC_UPD(FO, 2); break;    \
+        case 3: LINAC_UPD(FO, 3); break;    \
+        default: LINAC_UPD(FO, 0); break;   \
+    }
+    if (fold == 16) { LINAC_UPD_SH(16) }
+    else if (fold == 8) { LINAC_UPD_SH(8) }
+    else { LINAC_UPD_SH(4) }
+#undef LINAC_UPD_SH
+#undef LINAC_UPD
+}
+}  // namespace
 
 linac_status launch_update_limb(uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0, const Field& f,
                                 const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,
@@ -163,14 +218,9 @@ linac_status launch_update(int path, uint32_t* M, int64_t m, int64_t n, int64_t 
         return launch_update_limb(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, limb, stream);
     const int64_t ncols = n - c0;
     if (ncols <= 0 || m <= 0) return LINAC_OK;
-    dim3 grid((unsigned)((ncols + UPD_BN - 1) / UPD_BN), (unsigned)((m + UPD_BM - 1) / UPD_BM));
+    dim3 grid((unsigned)((ncols + UPD_BN2 - 1) / UPD_BN2), (unsigned)((m + UPD_BM - 1) / UPD_BM));
     ProfScope ps(stream, PROF_UPDATE_PLAIN);
-    if (f.fold >= 16)
-        update_plain_kernel<16, 0><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, nullptr, 0);
-    else if (f.fold >= 8)
-        update_plain_kernel<8, 0><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, nullptr, 0);
-    else
-        update_plain_kernel<4, 0><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, nullptr, 0);
+    launch_plain<0>(grid, stream, M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, nullptr, 0);
     LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;
 }
@@ -179,15 +229,10 @@ linac_status launch_gemm_assign(const Field& f, const DenseState* st, const int3
                                 const int32_t* W, int64_t ldW, int64_t ncols, int32_t* R, int64_t ldR,
                                 cudaStream_t stream) {
     if (ncols <= 0) return LINAC_OK;
-    dim3 grid((unsigned)((ncols + UPD_BN - 1) / UPD_BN), 1);
+    dim3 grid((unsigned)((ncols + UPD_BN2 - 1) / UPD_BN2), 1);
     ProfScope ps(stream, PROF_TRSM);
     // A rows are the NB_MAX columns of Et (zero beyond k); K runs to kpad(k)
-    if (f.fold >= 8)
-        update_plain_kernel<8, 1><<<grid, 256, 0, stream>>>(nullptr, NB_MAX, ncols, 0, 0, f, st, Et, ldE, W, ldW,
-                                                           R, ldR);
-    else
-        update_plain_kernel<4, 1><<<grid, 256, 0, stream>>>(nullptr, NB_MAX, ncols, 0, 0, f, st, Et, ldE, W, ldW,
-                                                           R, ldR);
+    launch_plain<1>(grid, stream, nullptr, NB_MAX, ncols, 0, 0, f, st, Et, ldE, W, ldW, R, ldR);
     LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;
 }
