@@ -48,7 +48,10 @@ UNIT = "field MAC/s"
 P31 = 2**31 - 1
 SMS = 152                 # GB300 SM count
 SM_MAX_MHZ = 2070.0       # GB300 maximum SM clock
-IMAD_LANES_PER_SM = 64    # 32-bit integer multiply-add lanes per SM per clock (4 x 16)
+# 64-bit-accumulating integer multiply-adds (mad.wide.s32) per SM per clock:
+# 4 schedulers x a 16-lane multiply pipe, two passes per wide multiply-add
+# (ncu: ~4 pipe cycles per 32-thread warp instruction on GB300)
+IMAD_WIDE_PER_SM_CLK = 32
 
 
 def parse():
@@ -293,9 +296,10 @@ def run_ours(args):
     upd_launches, upd_ms = prof.get(upd_name, (0, 0.0))
     upd_macs = update_work(m, n, piv, nb) * args.steps
     fold = fold_of(p)
-    imad_per_mac = 1.0 + 2.0 / fold
+    shift_fold = bin((1 << 32) % p).count("1") <= 3       # folds run on the ALU pipe
+    imad_per_mac = 1.0 if shift_fold else 1.0 + 2.0 / fold
     achieved = upd_macs / (upd_ms / 1000.0) if upd_ms else 0.0
-    peak = SMS * IMAD_LANES_PER_SM * SM_MAX_MHZ * 1e6 / imad_per_mac
+    peak = SMS * IMAD_WIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / imad_per_mac
     kernel_times = {k: {"launches": v[0], "total_ms": round(v[1], 3),
                         "share": round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4)}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -311,8 +315,9 @@ def run_ours(args):
         "roofline": {"kernel": upd_name, "bound": "alu", "achieved": achieved / 1e12,
                      "peak": peak / 1e12, "unit": "Tfield-MAC/s", "frac": achieved / peak if peak else None,
                      "traffic": None,
-                     "peak_basis": f"{SMS} SMs x {IMAD_LANES_PER_SM} IMAD/clk x {SM_MAX_MHZ:.0f} MHz / "
-                                   f"{imad_per_mac:.3f} IMAD per field MAC (fold every {fold})",
+                     "peak_basis": f"{SMS} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x {SM_MAX_MHZ:.0f} MHz"
+                                   f" / {imad_per_mac:.3f} per field MAC"
+                                   f" ({'folds on the ALU pipe' if shift_fold else f'fold every {fold} on the multiply pipe'})",
                      "avg_launch_ms": upd_ms / max(1, upd_launches), "launches": upd_launches},
         "gpu_launches": int(launches),
         "clocks": clocks,
