@@ -404,6 +404,7 @@ def batched_leg(args, linac, synth, dev, stream):
     rank-deficient), one linac_rref_batched call per step."""
     import torch
     B = synth.batched_uneven(count=args.batch_count)
+    widths = linac.linac_batched_tune(B.p)          # once per process, untimed
     data0 = torch.from_numpy(B.data.view(np.int32)).to(dev)
     data = torch.empty_like(data0)
     offs = torch.from_numpy(B.offsets).to(dev)
@@ -428,7 +429,7 @@ def batched_leg(args, linac, synth, dev, stream):
     ok = bool((rk == B.nA - B.deficiency).all())
     macs = sum((int(B.m[s]) - 1) * (int(B.n[s]) * int(rk[s]) - int(rk[s]) * (int(rk[s]) + 1) // 2)
                for s in range(B.count))
-    return {"systems": B.count, "systems_per_s": B.count / (ms / 1000.0), "ms": ms,
+    return {"systems": B.count, "systems_per_s": B.count / (ms / 1000.0), "ms": ms, "panel_widths": widths,
             "field_macs_per_s_approx": macs / (ms / 1000.0), "ranks_ok": ok,
             "workload": "batched uneven [A|B], n log-uniform [32,512], 4 RHS, p = 2^31 - 19"}
 
@@ -437,6 +438,7 @@ def shared_leg(args, linac, synth, dev, stream):
     """4096 evaluations of a 384 x 400 block-banded polynomial template."""
     import torch
     B = synth.shared_pattern(count=4096)
+    widths = linac.linac_batched_tune(B.p)
     data0 = torch.from_numpy(B.data.view(np.int32)).to(dev)
     data = torch.empty_like(data0)
     offs = torch.from_numpy(B.offsets).to(dev)
@@ -462,6 +464,7 @@ def shared_leg(args, linac, synth, dev, stream):
         out[name] = {"systems_per_s": B.count / (ms / 1000.0), "ms": ms,
                      "ranks_ok": bool((ranks.cpu().numpy() == 384).all())}
     out["speedup"] = out["search"]["ms"] / out["shared_pattern"]["ms"]
+    out["panel_widths"] = widths
     return out
 
 

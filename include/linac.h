@@ -183,6 +183,21 @@ linac_status linac_rref_batched(uint32_t *d_data, const int64_t *d_offsets,
                                 int32_t *d_ranks, int32_t *d_pivots, const int64_t *d_piv_offsets,
                                 int32_t *d_status, cudaStream_t stream);
 
+/*
+ * linac_batched_tune -- autotuner of linac_rref_batched's panel width per
+ * size bucket (row counts <= 64, 128, 256, 512, 1024).  For every bucket it
+ * times each panel width that fits the GPU's shared memory (16, 32, 64) on
+ * synthetic systems of that bucket's sizes (mod p) and keeps the fastest for
+ * the current device; later linac_rref_batched calls on this device use the
+ * table.  Allocates and frees its own buffers and synchronises `stream`: call
+ * it once at start-up, outside any stream capture.  nb_out (5 entries, may
+ * be NULL) receives the chosen widths.  Untuned buckets use 32.
+ */
+linac_status linac_batched_tune(uint32_t p, int32_t *nb_out, cudaStream_t stream);
+
+/* Current panel width per size bucket (5 entries). */
+linac_status linac_batched_panel_widths(int32_t *nb_out);
+
 /* Scratch bytes linac_rref_ex needs for an m x n problem with these options
  * (the library allocates them itself; exposed for capacity planning). */
 size_t linac_workspace_bytes(int64_t m, int64_t n, const linac_options *opts);

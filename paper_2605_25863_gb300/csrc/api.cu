@@ -259,6 +259,17 @@ linac_status linac_rref_batched(uint32_t* d_data, const int64_t* d_offsets, cons
                         d_ranks, d_pivots, d_piv_offsets, d_status, stream);
 }
 
+linac_status linac_batched_tune(uint32_t p, int32_t* nb_out, cudaStream_t stream) {
+    if (!prime_ok(p)) return LINAC_ERR_PRIME;
+    return batched_tune(make_field(p), nb_out, stream);
+}
+
+linac_status linac_batched_panel_widths(int32_t* nb_out) {
+    if (!nb_out) return LINAC_ERR_ARG;
+    batched_get_nb(nb_out);
+    return LINAC_OK;
+}
+
 size_t linac_workspace_bytes(int64_t m, int64_t n, const linac_options* opts) {
     if (m < 0 || n < 0) return 0;
     const int nb = opts && opts->nb ? opts->nb : dense_default_nb(m, n);

@@ -23,6 +23,7 @@
 #include <climits>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "linac_host.h"
 #include "profile.h"
@@ -82,25 +83,29 @@ batch_sort_kernel(const int32_t* __restrict__ dm, int batch, int32_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory layout of one block (sized by the bucket's largest m).
+// Shared-memory layout of one block (sized by the bucket's largest m).  The
+// panel slab is dead once the pivot rows' panel entries are copied out, so
+// the multipliers F and the column tiles reuse its space.
 
 struct BtLayout {
     int mmax, ldF;
-    size_t off_ft, off_p, off_pu, off_e, off_isp, total;
+    size_t off_p, off_ft, off_tiles, off_pu, off_e, off_isp, total;
 };
 
 __host__ __device__ inline BtLayout bt_layout(int mmax, int nb) {
     BtLayout L;
     L.mmax = mmax;
-    L.ldF = (mmax + 3) / 4 * 4;
-    size_t o = 0;
-    L.off_ft = o;  o += (size_t)nb * L.ldF * 4;                       // Ft[t][row], balanced
-    L.off_p = o;
-    const size_t panel = (size_t)mmax * (nb + 1) * 4;                  // panel slab
-    const size_t tiles = (size_t)3 * nb * BT_TB * 4;                   // V, X, R tiles
-    o += panel > tiles ? panel : tiles;
+    L.ldF = (mmax + 7) / 8 * 8;
+    const size_t panel = (size_t)mmax * (nb + 1) * 4;                 // panel slab
+    const size_t ftb = (size_t)nb * L.ldF * 4;                        // Ft[t][row], balanced
+    const size_t tiles = (size_t)3 * nb * BT_TB * 4;                  // V, X, R tiles
+    L.off_p = 0;
+    L.off_ft = 0;
+    L.off_tiles = ftb;
+    size_t o = panel > ftb + tiles ? panel : ftb + tiles;
+    o = (o + 15) / 16 * 16;
     L.off_pu = o;  o += (size_t)nb * nb * 4;                           // pivot rows' panel entries
-    L.off_e = o;   o += (size_t)nb * nb * 4;                           // E = G^{-1}
+    L.off_e = o;   o += (size_t)nb * nb * 4;                           // E^T = (G^{-1})^T, balanced
     L.off_isp = o; o += (size_t)((mmax + 15) / 16 * 16);              // pivot flags
     L.total = (o + 15) / 16 * 16;
     return L;
@@ -114,24 +119,38 @@ struct BtSmall {
     int s_min, s_sys, s_npairs, s_fail;
 };
 
-// Lowest index i in [0, cnt) with pred(i), block-wide (INT_MAX if none).
-template <int NB, typename Pred>
-__device__ __forceinline__ int block_first(int cnt, Pred pred, BtSmall<NB>& sm) {
-    int ci = INT_MAX;
-    for (int i = threadIdx.x; i < cnt; i += BT_THREADS)
-        if (pred(i)) { ci = i; break; }
-    for (int o = 16; o; o >>= 1) ci = min(ci, __shfl_xor_sync(0xffffffffu, ci, o));
+// Block-wide minimum of one int per thread (INT_MAX = none).
+template <int NB>
+__device__ __forceinline__ int block_min(int v, BtSmall<NB>& sm) {
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) sm.red[warp] = ci;
+    if (lane == 0) sm.red[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        int v = lane < BT_THREADS / 32 ? sm.red[lane] : INT_MAX;
-        for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) sm.s_min = v;
+        int x = lane < BT_THREADS / 32 ? sm.red[lane] : INT_MAX;
+        for (int o = 16; o; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (lane == 0) sm.s_min = x;
     }
     __syncthreads();
     return sm.s_min;
 }
+
+// Signed lazy accumulator fold: H*c32 + L, with H*c32 on the ALU pipe when
+// c32 = 2^32 mod p has at most three set bits (nshift > 0).
+__device__ __forceinline__ int64_t bt_fold(int64_t acc, const Field& f, int nshift, uint32_t e0, uint32_t e1,
+                                           uint32_t e2) {
+    if (nshift == 0) return fold64_fast(acc, f);
+    const int64_t h = acc >> 32;
+    int64_t r = (int64_t)(uint32_t)acc + (int64_t)((uint64_t)h << e0);
+    if (nshift > 1) r += (int64_t)((uint64_t)h << e1);
+    if (nshift > 2) r += (int64_t)((uint64_t)h << e2);
+    return r;
+}
+
+struct BtFold {
+    int nshift, mask;   // fold after products t with (t & mask) == mask
+    uint32_t e0, e1, e2;
+};
 
 // Reduce system A (m x n, leading dimension ld) in place.  mode 0: pivot
 // search; mode 1: reuse the probe's pattern (pat_J / pat_Pi / pat_k per
@@ -140,22 +159,28 @@ __device__ __forceinline__ int block_first(int cnt, Pred pred, BtSmall<NB>& sm) 
 // pivots.
 template <int NB>
 __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, int ns, const Field& f,
-                          int32_t* __restrict__ piv, int* rank_out, uint8_t* smem, const BtLayout& L,
-                          BtSmall<NB>& sm, int mode, const int32_t* pat_J, const int32_t* pat_Pi,
-                          const int* pat_k, int32_t* rec_J, int32_t* rec_Pi, int* rec_k) {
-    int32_t* Ft = (int32_t*)(smem + L.off_ft);
+                          const BtFold& fo, int32_t* __restrict__ piv, int* rank_out, uint8_t* smem,
+                          const BtLayout& L, BtSmall<NB>& sm, int mode, const int32_t* pat_J,
+                          const int32_t* pat_Pi, const int* pat_k, int32_t* rec_J, int32_t* rec_Pi, int* rec_k) {
     uint32_t* P = (uint32_t*)(smem + L.off_p);
+    int32_t* Ft = (int32_t*)(smem + L.off_ft);
+    uint32_t* V = (uint32_t*)(smem + L.off_tiles);
+    uint32_t* X = V + NB * BT_TB;
+    int32_t* Rt = (int32_t*)(V + 2 * NB * BT_TB);
     uint32_t* PU = (uint32_t*)(smem + L.off_pu);
-    uint32_t* E = (uint32_t*)(smem + L.off_e);
+    int32_t* Et = (int32_t*)(smem + L.off_e);
+    uint32_t* E = (uint32_t*)Et;
     unsigned char* isp = smem + L.off_isp;
-    uint32_t* V = P;                                  // tiles alias the panel slab
-    uint32_t* X = P + NB * BT_TB;
-    int32_t* Rt = (int32_t*)(P + 2 * NB * BT_TB);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = BT_THREADS / 32;
     const int SW = NB + 1;
+    const int ldF = L.ldF;
 
     const int npiv = min(m, ns);
     for (int i = tid; i < npiv; i += BT_THREADS) piv[i] = -1;
+    // 16-byte row accesses only when the system's start and rows are aligned
+    // (offsets and leading dimensions are device data the host cannot check)
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && ((ld & 3) == 0);
     int r = 0;
     int panel = 0;
     for (int c0 = 0; c0 < ns && r < m; c0 += NB, ++panel) {
@@ -169,27 +194,42 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
             }
             for (int i = tid; i < rows; i += BT_THREADS) isp[i] = 0;
             __syncthreads();
+            // candidate for the first column
+            int cand = INT_MAX;
+            for (int i = tid; i < rows; i += BT_THREADS)
+                if (P[i * SW] != 0) { cand = i; break; }
+            int q = block_min<NB>(cand, sm);
             for (int cc = 0; cc < w; ++cc) {
-                const int q = block_first<NB>(rows, [&](int i) { return !isp[i] && P[i * SW + cc] != 0; }, sm);
-                if (q == INT_MAX) continue;
-                if (tid == 0) {
-                    isp[q] = 1;
-                    sm.J[k] = c0 + cc;
-                    sm.Pi[k] = r + q;
-                    sm.own[k] = q;
+                // q: lowest non-pivot row with a nonzero entry in column cc
+                if (q != INT_MAX) {
+                    if (tid == 0) {
+                        isp[q] = 1;
+                        sm.J[k] = c0 + cc;
+                        sm.Pi[k] = r + q;
+                        sm.own[k] = q;
+                    }
+                    ++k;
                 }
-                const uint32_t h = P[q * SW + cc];
-                for (int i = tid / 32; i < rows; i += BT_THREADS / 32) {
+                // eliminate column cc (fraction-free) and look for the next
+                // column's candidate in the same pass over the rows
+                cand = INT_MAX;
+                const uint32_t h = q != INT_MAX ? P[q * SW + cc] : 0u;
+                for (int i = warp; i < rows; i += NW) {
                     if (i == q || isp[i]) continue;
                     uint32_t* row = P + i * SW;
-                    const uint32_t fi = row[cc];
-                    if (fi == 0) continue;
-                    const uint32_t nf = f.p - fi;
-                    for (int j = cc + 1 + (tid & 31); j < w; j += 32)
-                        row[j] = mul2add(h, row[j], nf, P[q * SW + j], f);
+                    if (q != INT_MAX) {
+                        const uint32_t fi = row[cc];
+                        if (fi != 0) {
+                            const uint32_t nf = f.p - fi;
+                            for (int j = cc + 1 + lane; j < w; j += 32)
+                                row[j] = mul2add(h, row[j], nf, P[q * SW + j], f);
+                        }
+                        __syncwarp();
+                    }
+                    if (cc + 1 < w && lane == 0 && row[cc + 1] != 0 && i < cand) cand = i;
                 }
-                ++k;
-                __syncthreads();
+                if (cc + 1 < w) q = block_min<NB>(cand, sm);
+                else __syncthreads();
             }
             for (int e = tid; e < k * w; e += BT_THREADS) {
                 const int t = e / w, j = e % w;
@@ -202,6 +242,7 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
                     rec_Pi[panel * NB + t] = sm.Pi[t];
                 }
             }
+            __syncthreads();   // P is dead from here on (F and the tiles reuse it)
         } else {
             // shared pattern: pivot rows and columns of the probe; eliminate the
             // k pivot rows among themselves (the same recurrence the search
@@ -222,12 +263,12 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
                 const int cs = sm.J[s] - c0;
                 const uint32_t h = PU[s * NB + cs];
                 if (h == 0) { if (tid == 0) sm.s_fail = 1; }
-                for (int t = s + 1 + tid / 32; t < k; t += BT_THREADS / 32) {
+                for (int t = s + 1 + warp; t < k; t += NW) {
                     uint32_t* row = PU + t * NB;
                     const uint32_t fi = row[cs];
                     if (fi == 0 || h == 0) continue;
                     const uint32_t nf = f.p - fi;
-                    for (int j = cs + 1 + (tid & 31); j < w; j += 32)
+                    for (int j = cs + 1 + lane; j < w; j += 32)
                         row[j] = mul2add(h, row[j], nf, PU[s * NB + j], f);
                 }
                 __syncthreads();
@@ -235,10 +276,12 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
             if (sm.s_fail) return false;
         }
         if (k == 0) continue;
-        // multipliers F (original entries at the pivot columns), inverses, E
+        // multipliers F (original entries at the pivot columns); loads unrolled
+        // so several are in flight per thread
+#pragma unroll 4
         for (int e = tid; e < k * m; e += BT_THREADS) {
-            const int t = e / m, i = e % m;
-            Ft[t * L.ldF + i] = to_balanced(A[(int64_t)i * ld + sm.J[t]], f);
+            const int t = e / m, i = e - t * m;
+            Ft[t * ldF + i] = to_balanced(A[(int64_t)i * ld + sm.J[t]], f);
         }
         for (int t = tid; t < k; t += BT_THREADS) {
             sm.hs[t] = PU[t * NB + (sm.J[t] - c0)];
@@ -286,62 +329,59 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
         }
         const int npairs = sm.s_npairs;
         for (int e = tid; e < npairs * k; e += BT_THREADS) {
-            const int a = e / k, t = e % k;
-            Ft[t * L.ldF + sm.dsts[a]] = Ft[t * L.ldF + sm.srcs[a]];
+            const int t = e / npairs, a = e % npairs;
+            Ft[t * ldF + sm.dsts[a]] = Ft[t * ldF + sm.srcs[a]];
         }
-        // E to balanced form for the tile products
-        for (int e = tid; e < k * k; e += BT_THREADS) {
-            const int t = e / k, j = e % k;
-            E[t * NB + j] = (uint32_t)to_balanced(E[t * NB + j], f);
+        // E^T in balanced form (register-tiled R = E V reads 4 consecutive t);
+        // kp = k rounded up to 4, with zero padding
+        const int kp = (k + 3) & ~3;
+        {
+            // transpose through registers: each thread owns whole (t, s) entries
+            uint32_t v[NB * NB / BT_THREADS + 1];
+            int cnt = 0;
+            for (int e = tid; e < kp * kp; e += BT_THREADS, ++cnt) {
+                const int t = e / kp, s2 = e % kp;
+                v[cnt] = (t < k && s2 < k) ? (uint32_t)to_balanced(E[t * NB + s2], f) : 0u;
+            }
+            __syncthreads();
+            cnt = 0;
+            for (int e = tid; e < kp * kp; e += BT_THREADS, ++cnt) {
+                const int t = e / kp, s2 = e % kp;
+                Et[s2 * NB + t] = (int32_t)v[cnt];
+            }
         }
         __syncthreads();
         // column tiles
         for (int j0 = c0; j0 < n; j0 += BT_TB) {
             const int tw = min(BT_TB, n - j0);
-            for (int e = tid; e < k * tw; e += BT_THREADS) {
-                const int t = e / tw, j = e % tw;
-                V[t * BT_TB + j] = (uint32_t)to_balanced(A[(int64_t)sm.Pi[t] * ld + j0 + j], f);
+#pragma unroll 4
+            for (int e = tid; e < kp * BT_TB; e += BT_THREADS) {
+                const int t = e / BT_TB, j = e % BT_TB;
+                V[t * BT_TB + j] = (t < k && j < tw) ? (uint32_t)to_balanced(A[(int64_t)sm.Pi[t] * ld + j0 + j], f) : 0u;
             }
             for (int e = tid; e < npairs * tw; e += BT_THREADS) {
                 const int a = e / tw, j = e % tw;
                 X[a * BT_TB + j] = A[(int64_t)sm.srcs[a] * ld + j0 + j];
             }
             __syncthreads();
-            // R = E V (balanced operands, lazy signed accumulation)
-            for (int e = tid; e < k * tw; e += BT_THREADS) {
-                const int t = e / tw, j = e % tw;
-                int64_t acc = 0;
-                for (int s = 0; s < k; ++s) {
-                    mac_s64(acc, (int32_t)E[t * NB + s], (int32_t)V[s * BT_TB + j]);
-                    if ((s & 3) == 3) acc = fold64_fast(acc, f);
-                }
-                Rt[t * BT_TB + j] = to_balanced(reduce_signed(acc, f), f);
-            }
-            for (int e = tid; e < npairs * tw; e += BT_THREADS) {
-                const int a = e / tw, j = e % tw;
-                A[(int64_t)sm.dsts[a] * ld + j0 + j] = X[a * BT_TB + j];
-            }
-            __syncthreads();
-            // update: rows in [r, r+k) receive R, every other row A -= F R
-            const int rgroups = (m + 3) / 4;
-            const int cq = (tw + 3) / 4;
-            for (int e = tid; e < rgroups * cq; e += BT_THREADS) {
-                const int d0 = (e / cq) * 4, jq = (e % cq) * 4;
+            // R = E V, 4 x 4 outputs per thread (balanced operands, lazy signed accumulation)
+            for (int e = tid; e < (kp / 4) * (BT_TB / 4); e += BT_THREADS) {
+                const int t0 = (e / (BT_TB / 4)) * 4, jq = (e % (BT_TB / 4)) * 4;
                 int64_t acc[4][4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
                     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-                for (int t = 0; t < k; ++t) {
-                    const int4 fv = *reinterpret_cast<const int4*>(Ft + t * L.ldF + d0);
-                    const int4 rv = *reinterpret_cast<const int4*>(Rt + t * BT_TB + jq);
-                    const int fa[4] = {fv.x, fv.y, fv.z, fv.w};
-                    const int rb[4] = {rv.x, rv.y, rv.z, rv.w};
+                for (int s2 = 0; s2 < kp; ++s2) {
+                    const int4 ev = *reinterpret_cast<const int4*>(Et + s2 * NB + t0);
+                    const int4 vv = *reinterpret_cast<const int4*>(V + s2 * BT_TB + jq);
+                    const int ea[4] = {ev.x, ev.y, ev.z, ev.w};
+                    const int vb[4] = {vv.x, vv.y, vv.z, vv.w};
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) mac_s64(acc[a][b], fa[a], rb[b]);
-                    if ((t & 3) == 3) {
+                        for (int b = 0; b < 4; ++b) acc[a][b] += (int64_t)ea[a] * vb[b];
+                    if ((s2 & fo.mask) == fo.mask) {
 #pragma unroll
                         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -349,21 +389,90 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
                     }
                 }
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) Rt[(t0 + a) * BT_TB + jq + b] = to_balanced(reduce_signed(acc[a][b], f), f);
+            }
+            for (int e = tid; e < npairs * tw; e += BT_THREADS) {
+                const int a = e / tw, j = e % tw;
+                A[(int64_t)sm.dsts[a] * ld + j0 + j] = X[a * BT_TB + j];
+            }
+            __syncthreads();
+            // update: rows in [r, r+k) receive R, every other row A -= F R
+            // (MR rows x 4 columns per work item; MR = 8 for 64-column panels,
+            // whose blocks own an SM alone, 4 otherwise so two blocks fit)
+            constexpr int MR = NB >= 64 ? 8 : 4;
+            const int rgroups = (m + MR - 1) / MR;
+            constexpr int cq = BT_TB / 4;
+            for (int e = tid; e < rgroups * cq; e += BT_THREADS) {
+                const int d0 = (e / cq) * MR, jq = (e % cq) * 4;
+                if (jq >= tw) continue;
+                // prefetch the item's current values so their latency overlaps the products
+                uint4 cur[MR];
+#pragma unroll
+                for (int a = 0; a < MR; ++a) {
+                    const int d = d0 + a;
+                    const uint32_t* rowp = A + (int64_t)d * ld + j0 + jq;
+                    if (d < m && jq + 4 <= tw && vec_ok) cur[a] = *reinterpret_cast<const uint4*>(rowp);
+                    else if (d < m) {
+                        cur[a].x = rowp[0];
+                        cur[a].y = jq + 1 < tw ? rowp[1] : 0u;
+                        cur[a].z = jq + 2 < tw ? rowp[2] : 0u;
+                        cur[a].w = jq + 3 < tw ? rowp[3] : 0u;
+                    } else cur[a] = make_uint4(0u, 0u, 0u, 0u);
+                }
+                int64_t acc[MR][4];
+#pragma unroll
+                for (int a = 0; a < MR; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+                for (int t = 0; t < k; ++t) {
+                    int fa[MR];
+                    {
+                        const int4 f0 = *reinterpret_cast<const int4*>(Ft + t * ldF + d0);
+                        fa[0] = f0.x; fa[1] = f0.y; fa[2] = f0.z; fa[3] = f0.w;
+                        if (MR == 8) {
+                            const int4 f1 = *reinterpret_cast<const int4*>(Ft + t * ldF + d0 + (MR - 4));
+                            fa[MR - 4] = f1.x; fa[MR - 3] = f1.y; fa[MR - 2] = f1.z; fa[MR - 1] = f1.w;
+                        }
+                    }
+                    const int4 rv = *reinterpret_cast<const int4*>(Rt + t * BT_TB + jq);
+                    const int rb[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                    for (int a = 0; a < MR; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] += (int64_t)fa[a] * rb[b];
+                    if ((t & fo.mask) == fo.mask) {
+#pragma unroll
+                        for (int a = 0; a < MR; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) acc[a][b] = fold64_fast(acc[a][b], f);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < MR; ++a) {
                     const int d = d0 + a;
                     if (d >= m) continue;
                     uint32_t* row = A + (int64_t)d * ld + j0;
                     const bool prow = d >= r && d < r + k;
+                    const uint32_t c4[4] = {cur[a].x, cur[a].y, cur[a].z, cur[a].w};
+                    uint32_t o4[4];
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const int j = jq + b;
-                        if (j >= tw) continue;
-                        uint32_t v;
-                        if (prow) v = from_balanced(Rt[(d - r) * BT_TB + j], f);
-                        else v = submod(row[j], reduce_signed(acc[a][b], f), f);
-                        row[j] = v;
+                        uint32_t v = 0;
+                        if (j < tw) {
+                            if (prow) v = from_balanced(Rt[(d - r) * BT_TB + j], f);
+                            else v = submod(c4[b], reduce_signed(acc[a][b], f), f);
+                        }
+                        o4[b] = v;
                         // shared pattern: rows below the new rank must vanish in the panel
-                        if (mode == 1 && d >= r + k && j0 + j < c0 + w && v != 0) sm.s_fail = 1;
+                        if (mode == 1 && d >= r + k && j < tw && j0 + j < c0 + w && v != 0) sm.s_fail = 1;
+                    }
+                    if (jq + 4 <= tw && vec_ok) {
+                        *reinterpret_cast<uint4*>(row + jq) = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+                    } else {
+                        for (int b = 0; b < 4 && jq + b < tw; ++b) row[jq + b] = o4[b];
                     }
                 }
             }
@@ -399,13 +508,13 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
 // Persistent kernel over one bucket.  pass 0: the bucket's systems (search,
 // or the shared pattern); pass 1: systems that failed the pattern (search).
 template <int NB>
-__global__ void __launch_bounds__(BT_THREADS)
+__global__ void __launch_bounds__(BT_THREADS, NB >= 64 ? 1 : 2)
 batched_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ offsets, const int32_t* __restrict__ dm,
                const int32_t* __restrict__ dn, const int32_t* __restrict__ dld, const int32_t* __restrict__ dns,
                const int32_t* __restrict__ order, int bucket, int mmax, Field f, int32_t* __restrict__ ranks,
                int32_t* __restrict__ pivots, const int64_t* __restrict__ piv_off, int32_t* __restrict__ sys_status,
                BatchScratch* bs, int pass, int use_pattern, const int32_t* pat_J, const int32_t* pat_Pi,
-               int32_t* fallback) {
+               int32_t* fallback, BtFold fo) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ BtSmall<NB> sm;
     const BtLayout L = bt_layout(mmax, NB);
@@ -440,11 +549,11 @@ batched_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ offsets,
             ok = false;
             if (threadIdx.x == 0) fallback[atomicAdd(&bs->nfallback, 1)] = s;
         } else if (use_pattern && pass == 0) {
-            ok = bt_reduce<NB>(A, m, n, dld[s], ns, f, piv, &rank, smem, L, sm, 1, pat_J, pat_Pi,
+            ok = bt_reduce<NB>(A, m, n, dld[s], ns, f, fo, piv, &rank, smem, L, sm, 1, pat_J, pat_Pi,
                                bs->pattern_k, nullptr, nullptr, nullptr);
             if (!ok && threadIdx.x == 0) fallback[atomicAdd(&bs->nfallback, 1)] = s;
         } else {
-            ok = bt_reduce<NB>(A, m, n, dld[s], ns, f, piv, &rank, smem, L, sm, 0, nullptr, nullptr, nullptr,
+            ok = bt_reduce<NB>(A, m, n, dld[s], ns, f, fo, piv, &rank, smem, L, sm, 0, nullptr, nullptr, nullptr,
                                nullptr, nullptr, nullptr);
         }
         __syncthreads();
@@ -463,7 +572,7 @@ batched_probe_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ of
                      const int32_t* __restrict__ dn, const int32_t* __restrict__ dld, const int32_t* __restrict__ dns,
                      int mmax, Field f, int32_t* __restrict__ ranks, int32_t* __restrict__ pivots,
                      const int64_t* __restrict__ piv_off, int32_t* __restrict__ sys_status, BatchScratch* bs,
-                     int32_t* pat_J, int32_t* pat_Pi) {
+                     int32_t* pat_J, int32_t* pat_Pi, BtFold fo) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ BtSmall<NB> sm;
     const BtLayout L = bt_layout(mmax, NB);
@@ -472,7 +581,7 @@ batched_probe_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ of
     for (int i = threadIdx.x; i < 1024 / 16 + 1; i += BT_THREADS) bs->pattern_k[i] = 0;
     __syncthreads();
     int rank = 0;
-    bt_reduce<NB>(data + offsets[0], m, n, dld[0], ns, f, pivots + piv_off[0], &rank, smem, L, sm, 0, nullptr,
+    bt_reduce<NB>(data + offsets[0], m, n, dld[0], ns, f, fo, pivots + piv_off[0], &rank, smem, L, sm, 0, nullptr,
                   nullptr, nullptr, pat_J, pat_Pi, bs->pattern_k);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -493,7 +602,25 @@ std::mutex g_bt_mu;
 int g_bt_nb[64][BT_NBUCKETS];   // 0 = default
 }
 
-static int bt_default_nb(int b) { return b >= 4 ? 16 : 32; }
+static int bt_default_nb(int b) { (void)b; return 32; }
+
+static BtFold bt_fold_params(const Field& f) {
+    BtFold fo;
+    fo.mask = f.fold >= 8 ? 7 : 3;
+    uint32_t e[3] = {0, 0, 0};
+    int n = 0;
+    bool ok = true;
+    for (int b = 0; b < 32; ++b)
+        if ((f.c32 >> b) & 1u) {
+            if (n == 3) { ok = false; break; }
+            e[n++] = (uint32_t)b;
+        }
+    fo.nshift = ok ? n : 0;
+    fo.e0 = e[0];
+    fo.e1 = e[1];
+    fo.e2 = e[2];
+    return fo;
+}
 
 int bt_bucket_nb(int b) {
     int dev = 0;
@@ -528,7 +655,8 @@ static linac_status launch_bucket(int b, int pass, int use_pattern, uint32_t* d_
     ProfScope ps(stream, use_pattern ? PROF_PATTERN : PROF_BATCHED);
     batched_kernel<NB><<<grid, BT_THREADS, L.total, stream>>>(d_data, d_offsets, d_m, d_n, d_ld, d_nsearch, order, b,
                                                               mmax, f, d_ranks, d_pivots, d_piv_offsets, d_status, bs,
-                                                              pass, use_pattern, pat_J, pat_Pi, fallback);
+                                                              pass, use_pattern, pat_J, pat_Pi, fallback,
+                                                              bt_fold_params(f));
     LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;
 }
@@ -597,7 +725,8 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
                                             (int)L.total));                                                     \
         batched_probe_kernel<NBV><<<1, BT_THREADS, L.total, stream>>>(d_data, d_offsets, d_m, d_n, d_ld, d_nsearch, \
                                                                       bt_bucket_max(top), f, d_ranks, d_pivots,  \
-                                                                      d_piv_offsets, d_status, bs, pat_J, pat_Pi); \
+                                                                      d_piv_offsets, d_status, bs, pat_J, pat_Pi,  \
+                                                                      bt_fold_params(f));                          \
         break;
             LINAC_PROBE(16)
             LINAC_PROBE(32)
@@ -623,6 +752,127 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
         }
     }
     return LINAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: per size bucket, time every feasible panel width on synthetic
+// systems of that bucket's sizes and keep the fastest for this device.
+
+namespace {
+
+// Uniform residues from a counter hash (SplitMix64 finaliser), for timing only.
+__global__ void tune_fill_kernel(uint32_t* data, int64_t words, uint32_t p, uint64_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        data[i] = (uint32_t)(((z >> 32) * (uint64_t)p) >> 32);
+    }
+}
+
+}  // namespace
+
+linac_status batched_tune(const Field& f, int32_t* nb_out, cudaStream_t stream) {
+    int max_smem = 0;
+    LINAC_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
+    const int cands[3] = {16, 32, 64};
+    for (int b = 0; b < BT_NBUCKETS; ++b) {
+        const int hi = bt_bucket_max(b), lo = b ? bt_bucket_max(b - 1) + 1 : 8;
+        // sizes spread over the bucket; enough systems to fill every SM several
+        // times (throughput, not single-system latency, is what is tuned), and
+        // at least a few ms of work, within a bounded footprint
+        std::vector<int> ms;
+        const double target = 4e9;                  // field multiply-adds per trial
+        const int min_count = 6 * sm_count();
+        const int64_t max_words = (int64_t)1 << 28;  // 1 GiB per copy
+        int64_t work = 0, wsum = 0;
+        for (int i = 0; (work < target || i < min_count) && i < 16384; ++i) {
+            const int mm = lo + (int)((int64_t)(hi - lo) * ((i * 37) % 101) / 100);
+            const int64_t wds = (int64_t)mm * ((mm + 4 + 3) / 4 * 4);
+            if (wsum + wds > max_words) break;
+            ms.push_back(mm);
+            wsum += wds;
+            work += (int64_t)mm * mm * mm / 2;
+        }
+        const int batch = (int)ms.size();
+        std::vector<int64_t> off(batch), poff(batch);
+        std::vector<int32_t> hm(batch), hn(batch), hld(batch), hns(batch);
+        int64_t words = 0, pw = 0;
+        for (int i = 0; i < batch; ++i) {
+            hm[i] = ms[i];
+            hns[i] = ms[i];
+            hn[i] = ms[i] + 4;
+            hld[i] = (hn[i] + 3) / 4 * 4;
+            off[i] = words;
+            words += (int64_t)hm[i] * hld[i];
+            poff[i] = pw;
+            pw += std::min(hm[i], hns[i]);
+        }
+        uint32_t *d_data = nullptr, *d_pristine = nullptr;
+        int64_t *d_off = nullptr, *d_poff = nullptr;
+        int32_t *d_m = nullptr, *d_n = nullptr, *d_ld = nullptr, *d_ns = nullptr, *d_ranks = nullptr, *d_piv = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        linac_status st = LINAC_OK;
+        auto bail = [&](linac_status s2) { st = s2; };
+        do {
+            if (cudaMalloc(&d_data, words * 4) || cudaMalloc(&d_pristine, words * 4) ||
+                cudaMalloc(&d_off, batch * 8) || cudaMalloc(&d_poff, batch * 8) || cudaMalloc(&d_m, batch * 4) ||
+                cudaMalloc(&d_n, batch * 4) || cudaMalloc(&d_ld, batch * 4) || cudaMalloc(&d_ns, batch * 4) ||
+                cudaMalloc(&d_ranks, batch * 4) || cudaMalloc(&d_piv, std::max<int64_t>(pw, 1) * 4)) {
+                bail(LINAC_ERR_NOMEM);
+                break;
+            }
+            cudaMemcpyAsync(d_off, off.data(), batch * 8, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync(d_poff, poff.data(), batch * 8, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync(d_m, hm.data(), batch * 4, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync(d_n, hn.data(), batch * 4, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync(d_ld, hld.data(), batch * 4, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync(d_ns, hns.data(), batch * 4, cudaMemcpyHostToDevice, stream);
+            tune_fill_kernel<<<1024, 256, 0, stream>>>(d_pristine, words, f.p, 0x5EEDull + b);
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            float best = 1e30f;
+            int best_nb = bt_default_nb(b);
+            for (int c = 0; c < 3; ++c) {
+                const int nb = cands[c];
+                if (bt_shared_bytes(b, nb) + 4096 > (size_t)max_smem) continue;
+                bt_set_bucket_nb(b, nb);
+                float t = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaMemcpyAsync(d_data, d_pristine, words * 4, cudaMemcpyDeviceToDevice, stream);
+                    cudaEventRecord(e0, stream);
+                    linac_status s2 = batched_rref(d_data, d_off, d_m, d_n, d_ld, d_ns, batch, hi, hi + 4, f, 0,
+                                                   d_ranks, d_piv, d_poff, nullptr, stream);
+                    cudaEventRecord(e1, stream);
+                    if (s2 != LINAC_OK) { t = 1e30f; break; }
+                    cudaEventSynchronize(e1);
+                    float ms_ = 0.f;
+                    cudaEventElapsedTime(&ms_, e0, e1);
+                    if (rep > 0) t = std::min(t, ms_);   // first run warms up
+                }
+                if (t < best) {
+                    best = t;
+                    best_nb = nb;
+                }
+            }
+            bt_set_bucket_nb(b, best_nb);
+            if (nb_out) nb_out[b] = best_nb;
+            if (cudaGetLastError() != cudaSuccess) bail(LINAC_ERR_CUDA);
+        } while (0);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaStreamSynchronize(stream);
+        for (void* ptr : {(void*)d_data, (void*)d_pristine, (void*)d_off, (void*)d_poff, (void*)d_m, (void*)d_n,
+                          (void*)d_ld, (void*)d_ns, (void*)d_ranks, (void*)d_piv})
+            if (ptr) cudaFree(ptr);
+        if (st != LINAC_OK) return st;
+    }
+    return LINAC_OK;
+}
+
+void batched_get_nb(int32_t* nb_out) {
+    for (int b = 0; b < BT_NBUCKETS; ++b) nb_out[b] = bt_bucket_nb(b);
 }
 
 }  // namespace linac

@@ -73,4 +73,9 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
                           uint32_t flags, int32_t* d_ranks, int32_t* d_pivots,
                           const int64_t* d_piv_offsets, int32_t* d_status, cudaStream_t stream);
 
+// Batched autotuner (batched.cu): per size bucket (m <= 64, 128, 256, 512,
+// 1024) time the feasible panel widths and keep the fastest for this device.
+linac_status batched_tune(const Field& f, int32_t* nb_out, cudaStream_t stream);
+void batched_get_nb(int32_t* nb_out);
+
 }  // namespace linac

@@ -84,6 +84,10 @@ def lib():
         L.linac_profile_read.restype = ctypes.c_int
         L.linac_measure_int_rates.argtypes = [ctypes.POINTER(IntRates), vp]
         L.linac_measure_int_rates.restype = ctypes.c_int
+        L.linac_batched_tune.argtypes = [ctypes.c_uint32, ctypes.c_void_p, vp]
+        L.linac_batched_tune.restype = ctypes.c_int
+        L.linac_batched_panel_widths.argtypes = [ctypes.c_void_p]
+        L.linac_batched_panel_widths.restype = ctypes.c_int
         L.linac_launch_count.argtypes = []
         L.linac_launch_count.restype = ctypes.c_longlong
         for name in ("linac_rref", "linac_rref_ex", "linac_solve", "linac_solve_ex",
@@ -241,3 +245,16 @@ def linac_measure_int_rates(stream=None) -> dict:
     r = IntRates()
     _check(lib().linac_measure_int_rates(ctypes.byref(r), _stream_ptr(stream)), "linac_measure_int_rates")
     return {k: getattr(r, k) for k, _ in IntRates._fields_}
+
+
+def linac_batched_tune(p: int, stream=None) -> list[int]:
+    """Autotune linac_rref_batched's panel width per size bucket (see include/linac.h)."""
+    out = (ctypes.c_int32 * 5)()
+    _check(lib().linac_batched_tune(p, out, _stream_ptr(stream)), "linac_batched_tune")
+    return list(out)
+
+
+def linac_batched_panel_widths() -> list[int]:
+    out = (ctypes.c_int32 * 5)()
+    _check(lib().linac_batched_panel_widths(out), "linac_batched_panel_widths")
+    return list(out)

@@ -136,3 +136,13 @@ def test_workload_shared_pattern_4096_sampled():
     check_all(B, B.p, out, ranks, piv, poff, which=sample)
     out2, ranks2, piv2, poff2, st2 = run_batched(B, B.p, flags=0)
     assert np.array_equal(out, out2) and np.array_equal(ranks, ranks2)
+
+
+def test_autotuned_widths_keep_parity():
+    """The autotuner picks a panel width per size bucket; results stay exact."""
+    widths = linac.linac_batched_tune(synth.P_BATCH)
+    assert len(widths) == 5 and all(w in (16, 32, 64) for w in widths)
+    assert linac.linac_batched_panel_widths() == widths
+    B = synth.batched_uneven(count=60, lo=8, hi=1000, seed=33, deficient_frac=0.3)
+    out, ranks, piv, poff, st = run_batched(B, B.p)
+    check_all(B, B.p, out, ranks, piv, poff)
