@@ -78,6 +78,28 @@ __global__ void finish_kernel(DenseState* st, int32_t* d_pivots, int32_t* d_rank
 // Shared memory: S_max x (w+1) residues (the slab, padded against bank
 // conflicts), the broadcast pivot row, the owned-pivot list and pivot flags.
 
+// Block-wide minimum of one int per thread.
+__device__ __forceinline__ int panel_block_min(int v, int* red, int* out) {
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < (int)(blockDim.x >> 5) ? red[lane] : INT_MAX;
+        for (int o = 16; o; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (lane == 0) *out = x;
+    }
+    __syncthreads();
+    return *out;
+}
+
+// Column-level look-ahead: for every column the block (1) applies the current
+// pivot to the next column only and searches it, (2) lets warp 0 finish its
+// candidate row, publish it and arrive at the grid barrier, and (3) while
+// warp 0 waits, lets the other warps apply the current pivot to the rest of
+// the panel, so the barrier latency overlaps the bulk of the elimination.
+// All arithmetic is the same fraction-free step as in the plain loop:
+// row_i <- h row_i - f_i pivot with f_i kept in column cc.
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, int S_max,
              Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status) {
@@ -88,10 +110,11 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
     int* own = (int*)(prow + NB_MAX);
     unsigned char* isp = (unsigned char*)(own + NB_MAX);
     __shared__ int s_red[PANEL_THREADS / 32];
-    __shared__ int s_min;
+    __shared__ int s_min, s_q, s_ok;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int G = gridDim.x, b = blockIdx.x;
+    int* cidx = (int*)(cand + (size_t)2 * G * NB_MAX);   // [2][G] candidate row per block
     const int64_t r = st->r;
     const int64_t left = m - r;
     const int S = left > 0 ? (int)((left + G - 1) / G) : 0;
@@ -105,59 +128,117 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
     }
     for (int i = tid; i < nrows; i += blockDim.x) isp[i] = 0;
     for (int t = tid; t < NB_MAX; t += blockDim.x) own[t] = -1;
+    if (tid == 0) s_ok = 1;
     __syncthreads();
 
-    int kk = 0;
-    for (int cc = 0; cc < w; ++cc) {
-        // lowest local non-pivot row with a nonzero entry in column cc
-        int ci = INT_MAX;
-        for (int i = tid; i < nrows; i += blockDim.x)
-            if (!isp[i] && P[i * SW + cc] != 0) { ci = i; break; }
-        for (int o = 16; o; o >>= 1) ci = min(ci, __shfl_xor_sync(0xffffffffu, ci, o));
-        if (lane == 0) s_red[warp] = ci;
-        __syncthreads();
-        if (warp == 0) {
-            int v = lane < nwarps ? s_red[lane] : INT_MAX;
-            for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if (lane == 0) s_min = v;
-        }
-        __syncthreads();
-        const int imin = s_min;
-        const int par = cc & 1;
+    // Publish this block's candidate (row imin, already fully updated) for
+    // column c0 + col and wait for every block.  Warp 0 only.
+    auto publish_and_wait = [&](int col, int imin) {
+        const int par = col & 1;
         if (imin != INT_MAX) {
-            // publish this block's candidate row before arriving at the barrier;
-            // buffers alternate by column parity so a candidate is never
-            // overwritten while another block may still read it
             uint32_t* dst = cand + ((size_t)par * G + b) * NB_MAX;
-            for (int j = tid; j < w; j += blockDim.x) dst[j] = P[imin * SW + j];
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) atomicMin(&st->best[cc], (int)(lo + imin));
+            for (int j = lane; j < w; j += 32) dst[j] = P[imin * SW + j];
         }
-        if (!grid_sync(&st->bar, (unsigned)G, status)) return;
-        const int q = __ldcg(&st->best[cc]);
-        if (q == INT_MAX) continue;   // no pivot in this column (uniform branch)
-        const int owner = (int)((q - r) / S);
-        const uint32_t* src = cand + ((size_t)par * G + owner) * NB_MAX;
-        for (int j = tid; j < w; j += blockDim.x) prow[j] = __ldcg(src + j);
-        if (tid == 0) {
-            if (b == owner) { isp[q - lo] = 1; own[kk] = (int)(q - lo); }
-            if (b == 0) { st->Pi[kk] = q; st->J[kk] = c0 + cc; }
+        if (lane == 0) cidx[par * G + b] = imin != INT_MAX ? (int)(lo + imin) : INT_MAX;
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            unsigned int* counter = &st->bar.count;
+            const unsigned int target = (unsigned)(c0 + col + 1) * (unsigned)G;
+            asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
+            const long long t0 = clock64();
+            for (unsigned int it = 0;; ++it) {
+                unsigned int v;
+                asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+                if ((int)(v - target) >= 0) break;
+                if ((it & 255u) == 255u) {
+                    if (*(volatile int*)status != 0) { s_ok = 0; break; }
+                    if (clock64() - t0 > kSpinCycles) {
+                        atomicCAS(status, 0, (int)LINAC_ERR_TIMEOUT);
+                        s_ok = 0;
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+        }
+        __syncwarp();
+    };
+    // After a __syncthreads that follows publish_and_wait: the pivot of
+    // column c0 + col (lowest candidate over all blocks), its row in prow.
+    int kk = 0;
+    auto take_winner = [&](int col) -> int {
+        const int par = col & 1;
+        if (warp == 0) {
+            int v = INT_MAX;
+            for (int g = lane; g < G; g += 32) v = min(v, __ldcg(&cidx[par * G + g]));
+            for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) s_q = v;
         }
         __syncthreads();
-        const uint32_t h = prow[cc];
-        // fraction-free elimination of column cc from the other non-pivot
-        // rows; the multiplier f stays stored in column cc
-        for (int i = warp; i < nrows; i += nwarps) {
+        const int q = s_q;
+        if (q != INT_MAX) {
+            const int owner = (int)((q - r) / S);
+            const uint32_t* src = cand + ((size_t)par * G + owner) * NB_MAX;
+            for (int j = tid; j < w; j += blockDim.x) prow[j] = __ldcg(src + j);
+            if (tid == 0) {
+                if (b == owner) { isp[q - lo] = 1; own[kk] = (int)(q - lo); }
+                if (b == 0) { st->Pi[kk] = q; st->J[kk] = c0 + col; }
+            }
+            ++kk;
+            __syncthreads();
+        }
+        return q;
+    };
+
+    // column 0: search, publish, take the pivot
+    int ci = INT_MAX;
+    for (int i = tid; i < nrows; i += blockDim.x)
+        if (P[i * SW] != 0) { ci = i; break; }
+    int imin = panel_block_min(ci, s_red, &s_min);
+    if (warp == 0) publish_and_wait(0, imin);
+    __syncthreads();
+    if (!s_ok) return;
+    int q = take_winner(0);
+
+    for (int cc = 0; cc + 1 < w; ++cc) {
+        const uint32_t h = q != INT_MAX ? prow[cc] : 0u;
+        // narrow update: column cc+1 only, with the search for its candidate
+        ci = INT_MAX;
+        for (int i = tid; i < nrows; i += blockDim.x) {
             if (isp[i]) continue;
             uint32_t* row = P + i * SW;
-            const uint32_t fi = row[cc];
-            if (fi == 0) continue;
-            const uint32_t nf = f.p - fi;
-            for (int j = cc + 1 + lane; j < w; j += 32) row[j] = mul2add(h, row[j], nf, prow[j], f);
+            if (q != INT_MAX) {
+                const uint32_t fi = row[cc];
+                if (fi != 0) row[cc + 1] = mul2add(h, row[cc + 1], f.p - fi, prow[cc + 1], f);
+            }
+            if (row[cc + 1] != 0 && i < ci) ci = i;
         }
-        ++kk;
+        imin = panel_block_min(ci, s_red, &s_min);
+        if (warp == 0) {
+            // finish the candidate row, publish it and wait at the barrier
+            if (imin != INT_MAX && q != INT_MAX) {
+                uint32_t* row = P + imin * SW;
+                const uint32_t fi = row[cc];
+                if (fi != 0)
+                    for (int j = cc + 2 + lane; j < w; j += 32) row[j] = mul2add(h, row[j], f.p - fi, prow[j], f);
+                __syncwarp();
+            }
+            publish_and_wait(cc + 1, imin);
+        } else if (q != INT_MAX) {
+            // bulk update of the other rows while warp 0 waits
+            for (int i = warp - 1; i < nrows; i += nwarps - 1) {
+                if (isp[i] || i == imin) continue;
+                uint32_t* row = P + i * SW;
+                const uint32_t fi = row[cc];
+                if (fi == 0) continue;
+                const uint32_t nf = f.p - fi;
+                for (int j = cc + 2 + lane; j < w; j += 32) row[j] = mul2add(h, row[j], nf, prow[j], f);
+            }
+        }
         __syncthreads();
+        if (!s_ok) return;
+        q = take_winner(cc + 1);
     }
     for (int t = 0; t < kk; ++t) {
         const int i = own[t];
@@ -412,7 +493,7 @@ DenseLayout dense_layout(int64_t m, int64_t n, int G) {
     DenseLayout L;
     size_t o = 0;
     L.off_state = o; o = align_up(o + sizeof(DenseState), 256);
-    L.off_cand = o;  o = align_up(o + (size_t)2 * G * NB_MAX * 4, 256);
+    L.off_cand = o;  o = align_up(o + (size_t)2 * G * (NB_MAX + 1) * 4, 256);
     L.off_panel = o; o = align_up(o + (size_t)NB_MAX * NB_MAX * 4, 256);
     L.off_e = o;     o = align_up(o + (size_t)NB_MAX * NB_MAX * 4, 256);
     L.ldF = (int64_t)align_up((size_t)std::max<int64_t>(m, 1), 4);

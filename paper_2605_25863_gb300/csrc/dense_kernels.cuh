@@ -7,7 +7,7 @@
 
 namespace linac {
 
-constexpr int PANEL_THREADS = 256;   // block size of panel_kernel
+constexpr int PANEL_THREADS = 512;   // block size of panel_kernel
 constexpr int EINV_COLS = 8;         // columns of E = G^{-1} per einv_kernel block
 constexpr size_t EINV_SMEM = ((size_t)NB_MAX * (NB_MAX + 1) + (size_t)NB_MAX * EINV_COLS) * 4;
 

@@ -175,4 +175,37 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, in
     return s_ok != 0;
 }
 
+// Arrival barrier on a monotonically increasing counter: each block adds 1
+// once per round and waits until the counter reaches target (= rounds done x
+// blocks).  No reset step, so the critical path is one posted reduction and
+// the polling reads.  The caller has fenced its published data and passed a
+// __syncthreads; on return every thread of the block may read what other
+// blocks published before arriving.  Gives up (returns false) after about
+// kSpinCycles clocks or when the status word is already set.
+__device__ __forceinline__ bool grid_arrive_wait(unsigned int* counter, unsigned int target, int* status) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
+        int ok = 1;
+        const long long t0 = clock64();
+        for (unsigned int it = 0;; ++it) {
+            unsigned int v;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if ((it & 255u) == 255u) {
+                if (*(volatile int*)status != 0) { ok = 0; break; }
+                if (clock64() - t0 > kSpinCycles) {
+                    atomicCAS(status, 0, (int)LINAC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 }  // namespace linac

@@ -54,7 +54,7 @@ NoallocLayout noalloc_layout(int64_t m, int64_t n) {
     size_t o = 0;
     L.off_status = o; o = align_up(o + 256, 256);
     L.off_state = o;  o = align_up(o + sizeof(DenseState), 256);
-    L.off_cand = o;   o = align_up(o + (size_t)2 * kNoallocMaxGrid * NB_MAX * 4, 256);
+    L.off_cand = o;   o = align_up(o + (size_t)2 * kNoallocMaxGrid * (NB_MAX + 1) * 4, 256);
     L.off_panel = o;  o = align_up(o + (size_t)NB_MAX * NB_MAX * 4, 256);
     L.off_e = o;      o = align_up(o + (size_t)NB_MAX * NB_MAX * 4, 256);
     L.ldF = (int64_t)align_up((size_t)std::max<int64_t>(m, 1), 4);
