@@ -237,6 +237,12 @@ typedef struct {
     double dp4a_u8_mac_per_s;
     double sm_clock_khz;      /* nominal maximum SM clock */
     int sm_count;
+    /* one block of 512 threads per SM: warps 0-7 run mad.wide.s32, warps 8-15
+     * mma.sync u8; time with only the first group working, only the second,
+     * and both at once (ms) */
+    double coissue_imad_only_ms;
+    double coissue_imma_only_ms;
+    double coissue_both_ms;
 } linac_int_rates;
 
 linac_status linac_measure_int_rates(linac_int_rates *out, cudaStream_t stream);

@@ -66,6 +66,49 @@ __global__ void probe_imma_u8(int* out, uint32_t seed, int iters) {
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Co-issue: warps 0-7 run mad.wide.s32 chains (multiply pipe), warps 8-15
+// run mma.sync u8 (tensor pipe).  MODE 0: only the first group works,
+// 1: only the second, 2: both at once.
+template <int MODE>
+__global__ void __launch_bounds__(512, 1) probe_coissue(long long* out, int it_imad, int it_imma) {
+    const int warp = threadIdx.x >> 5;
+    long long s = 0;
+    if (warp < 8) {
+        if (MODE == 0 || MODE == 2) {
+            long long acc[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) acc[j] = threadIdx.x * 31 + j;
+            const int b = 0x12345 | 1;
+            for (int it = 0; it < it_imad; ++it) {
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int a = (int)(unsigned)acc[j];
+                    asm volatile("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc[j]) : "r"(a), "r"(b));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j++) s += acc[j];
+        }
+    } else if (MODE == 1 || MODE == 2) {
+        const uint32_t a0 = threadIdx.x * 3, a1 = a0 * 5, a2 = a0 * 7, a3 = a0 * 11, b0 = a0 * 13, b1 = a0 * 17;
+        int d[4][4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) d[c][0] = d[c][1] = d[c][2] = d[c][3] = 0;
+        for (int it = 0; it < it_imma; ++it) {
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+                asm volatile(
+                    "mma.sync.aligned.m16n8k32.row.col.s32.u8.u8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                    "{%0,%1,%2,%3};\n"
+                    : "+r"(d[c][0]), "+r"(d[c][1]), "+r"(d[c][2]), "+r"(d[c][3])
+                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) s += d[c][0] + d[c][1] + d[c][2] + d[c][3];
+    }
+    out[blockIdx.x * 512 + threadIdx.x] = s;
+}
+
 }  // namespace linac
 
 using namespace linac;
@@ -75,7 +118,7 @@ extern "C" linac_status linac_measure_int_rates(linac_int_rates* out, cudaStream
     const int nsm = sm_count();
     const int grid = nsm * 8, threads = 256, iters = 4096;
     void* buf = nullptr;
-    LINAC_CUDA_TRY(cudaMalloc(&buf, (size_t)grid * threads * 8));
+    LINAC_CUDA_TRY(cudaMalloc(&buf, (size_t)grid * threads * 8));   // >= nsm * 512 * 8 for the co-issue probe
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -96,6 +139,16 @@ extern "C" linac_status linac_measure_int_rates(linac_int_rates* out, cudaStream
     out->dp4a_u8_mac_per_s = lanes * iters * 8 * 4 / t;
     t = time_it([&](int it) { probe_imma_u8<<<grid, threads, 0, stream>>>((int*)buf, 1u, it); });
     out->imma_u8_mac_per_s = (double)grid * (threads / 32) * iters * 4 * 4096.0 / t;
+    {
+        // co-issue of the two pipes in one block per SM
+        const int ii = 2048, im = 1024;
+        out->coissue_imad_only_ms =
+            1e3 * time_it([&](int) { probe_coissue<0><<<nsm, 512, 0, stream>>>((long long*)buf, ii, im); });
+        out->coissue_imma_only_ms =
+            1e3 * time_it([&](int) { probe_coissue<1><<<nsm, 512, 0, stream>>>((long long*)buf, ii, im); });
+        out->coissue_both_ms =
+            1e3 * time_it([&](int) { probe_coissue<2><<<nsm, 512, 0, stream>>>((long long*)buf, ii, im); });
+    }
     int clk = 0;
     cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
     out->sm_clock_khz = clk;

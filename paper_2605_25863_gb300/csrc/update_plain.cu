@@ -27,17 +27,31 @@ namespace linac {
 // pipe, leaving the multiply pipe to the products (2^31 - 1 gives c32 = 2,
 // 2^31 - 19 gives c32 = 38).
 struct FoldShifts {
-    uint32_t e[3];
+    uint32_t e[3];   // shift of each set bit of c32
+    uint32_t s[3];   // arithmetic right shift giving the high word of h * 2^e
 };
 
 template <int SHIFTS>
 __device__ __forceinline__ int64_t fold_any(int64_t acc, const Field& f, const FoldShifts& fs) {
     if (SHIFTS == 0) return fold64_fast(acc, f);
-    const int64_t h = acc >> 32;                  // signed high word
-    int64_t r = (int64_t)(uint32_t)acc;           // low word
+    // acc = hi:lo; result = lo + sum_i sext(hi) * 2^e_i as a 64-bit carry chain
+    // of 32-bit shifts and adds, written out so it stays on the ALU pipe
+    uint32_t lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(acc));
+    uint32_t rlo = lo, rhi = 0;
 #pragma unroll
-    for (int i = 0; i < SHIFTS; ++i) r += (int64_t)((uint64_t)h << fs.e[i]);   // h * 2^e, two's complement
-    return r;
+    for (int i = 0; i < SHIFTS; ++i) {
+        asm("{\n\t.reg .u32 t, u;\n\t"
+            "shl.b32 t, %2, %3;\n\t"
+            "shr.s32 u, %2, %4;\n\t"
+            "add.cc.u32 %0, %0, t;\n\t"
+            "addc.u32 %1, %1, u;\n\t}"
+            : "+r"(rlo), "+r"(rhi)
+            : "r"(hi), "r"(fs.e[i]), "r"(fs.s[i]));
+    }
+    int64_t out;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(out) : "r"(rlo), "r"(rhi));
+    return out;
 }
 
 // MODE 0: trailing update of M (rows [r, r+k) receive R).  MODE 1: plain
@@ -179,6 +193,7 @@ int fold_shifts(const Field& f, FoldShifts* fs) {
             fs->e[n++] = (uint32_t)b;
         }
     for (int i = n; i < 3; ++i) fs->e[i] = 0;
+    for (int i = 0; i < 3; ++i) fs->s[i] = fs->e[i] == 0 ? 31u : 32u - fs->e[i];
     return n;
 }
 

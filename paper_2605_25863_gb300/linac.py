@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
 class IntRates(ctypes.Structure):
     _fields_ = [("imad_wide_per_s", ctypes.c_double), ("imma_u8_mac_per_s", ctypes.c_double),
                 ("dp4a_u8_mac_per_s", ctypes.c_double), ("sm_clock_khz", ctypes.c_double),
-                ("sm_count", ctypes.c_int)]
+                ("sm_count", ctypes.c_int), ("coissue_imad_only_ms", ctypes.c_double),
+                ("coissue_imma_only_ms", ctypes.c_double), ("coissue_both_ms", ctypes.c_double)]
 
 
 class ProfileEntry(ctypes.Structure):
