@@ -187,7 +187,14 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
         const int w = min(NB, ns - c0);
         int k = 0;
         if (mode == 0) {
-            const int rows = m - r;
+          // The pivots of a panel come from a window of the first w + 32
+          // remaining rows: the RREF does not depend on which rows supply the
+          // pivots, so if the window already yields one pivot per panel column
+          // the pivot columns are settled; otherwise the panel is redone over
+          // all remaining rows.
+          const int rows_all = m - r;
+          for (int rows = min(rows_all, w + 32);; rows = rows_all) {
+            k = 0;
             for (int e = tid; e < rows * w; e += BT_THREADS) {
                 const int i = e / w, j = e % w;
                 P[i * SW + j] = A[(int64_t)(r + i) * ld + c0 + j];
@@ -231,6 +238,9 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
                 if (cc + 1 < w) q = block_min<NB>(cand, sm);
                 else __syncthreads();
             }
+            if (k == w || rows == rows_all) break;
+            __syncthreads();
+          }
             for (int e = tid; e < k * w; e += BT_THREADS) {
                 const int t = e / w, j = e % w;
                 PU[t * NB + j] = P[sm.own[t] * SW + j];
