@@ -36,6 +36,15 @@ constexpr int BT_NBUCKETS = 5;         // m <= 64, 128, 256, 512, 1024
 // largest row count of bucket b: 64, 128, 256, 512, 1024
 __host__ __device__ constexpr int bt_bucket_max(int b) { return 64 << b; }
 constexpr int BT_FLAG_FALLBACK = 0x100;
+constexpr int BT_WINDOW = 16;         // rows of the pivot window beyond the panel width
+
+// The pivot window's slab: bt_win_rows rows of 2 NB + 1 words (NB panel
+// entries, NB coefficients over the pivot rows, one pad word against bank
+// conflicts), then two per-row scale factors.
+__host__ __device__ constexpr int bt_win_rows(int nb) { return nb + BT_WINDOW; }
+__host__ __device__ constexpr size_t bt_win_bytes(int nb) {
+    return ((size_t)bt_win_rows(nb) * (2 * nb + 1) + 2 * (size_t)bt_win_rows(nb)) * 4;
+}
 
 // Per-call device scratch of the batched driver.
 struct BatchScratch {
@@ -96,13 +105,14 @@ __host__ __device__ inline BtLayout bt_layout(int mmax, int nb) {
     BtLayout L;
     L.mmax = mmax;
     L.ldF = (mmax + 7) / 8 * 8;
-    const size_t panel = (size_t)mmax * (nb + 1) * 4;                 // panel slab
+    const size_t panel = (size_t)mmax * (nb + 1) * 4;                 // panel slab (all rows)
     const size_t ftb = (size_t)nb * L.ldF * 4;                        // Ft[t][row], balanced
     const size_t tiles = (size_t)3 * nb * BT_TB * 4;                  // V, X, R tiles
     L.off_p = 0;
     L.off_ft = 0;
     L.off_tiles = ftb;
     size_t o = panel > ftb + tiles ? panel : ftb + tiles;
+    if (o < bt_win_bytes(nb)) o = bt_win_bytes(nb);                  // pivot window slab
     o = (o + 15) / 16 * 16;
     L.off_pu = o;  o += (size_t)nb * nb * 4;                           // pivot rows' panel entries
     L.off_e = o;   o += (size_t)nb * nb * 4;                           // E^T = (G^{-1})^T, balanced
@@ -116,6 +126,7 @@ struct BtSmall {
     int J[NB], Pi[NB], own[NB], srcs[NB], dsts[NB];
     uint32_t hinv[NB], hs[NB];
     int red[BT_THREADS / 32];
+    int red2[2][BT_THREADS / 32];
     int s_min, s_sys, s_npairs, s_fail;
 };
 
@@ -135,6 +146,22 @@ __device__ __forceinline__ int block_min(int v, BtSmall<NB>& sm) {
     return sm.s_min;
 }
 
+// Block-wide minimum with one barrier: each warp posts its minimum in one of
+// two alternating slots and every thread reduces the posts itself.  A slot is
+// written again two calls later, after another barrier, when every thread has
+// read it.
+template <int NB>
+__device__ __forceinline__ int block_min1(int v, BtSmall<NB>& sm, int& buf) {
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) sm.red2[buf][threadIdx.x >> 5] = v;
+    __syncthreads();
+    int x = INT_MAX;
+#pragma unroll
+    for (int i = 0; i < BT_THREADS / 32; ++i) x = min(x, sm.red2[buf][i]);
+    buf ^= 1;
+    return x;
+}
+
 // Signed lazy accumulator fold: H*c32 + L, with H*c32 on the ALU pipe when
 // c32 = 2^32 mod p has at most three set bits (nshift > 0).
 __device__ __forceinline__ int64_t bt_fold(int64_t acc, const Field& f, int nshift, uint32_t e0, uint32_t e1,
@@ -151,6 +178,143 @@ struct BtFold {
     int nshift, mask;   // fold after products t with (t & mask) == mask
     uint32_t e0, e1, e2;
 };
+
+// Pivots and E = G^{-1} of one panel from a window of rows, by fraction-free
+// Gauss-Jordan elimination of the panel columns c0 .. c0+w-1 augmented with
+// each row's coefficients over the pivot rows (one block barrier per column).
+//
+// Window row i is A row r + i (forced = 0: pivot search, the lowest row with
+// a nonzero entry in the column) or A row sm.Pi[i] (forced = 1: the pivot rows
+// and columns sm.Pi[t], sm.J[t] of a previous search, in order; rows = k).
+// Every row keeps
+//     current row i = sig_i * (original row i) + sum_u a_iu * (original pivot row u)
+// with the coefficients a_iu in slab columns NB + u.  A column cc with a pivot
+// (row q, pivot number s, head h = row_q[cc]) sets a_qs = sig_q, then
+// replaces every other row i with f = row_i[cc] != 0 -- earlier pivot rows
+// included -- by h * row_i - f * row_q on the panel columns right of cc and on
+// the coefficients 0..s; the factor h also goes into sig_i, or into the head
+// hd_i of an earlier pivot row.  At the end pivot row t is zero at every other
+// pivot column and hd_t at its own, so E[t][u] = a_{t u} / hd_t gives E G = I.
+//
+// The w - cc - 1 panel columns and s + 1 <= cc + 1 coefficients that change
+// at column cc fit in NB slab columns, so the block is laid out as NB
+// columns by BT_THREADS / NB row groups, and column slot cp of a thread names
+// panel column cc + 1 + cp, or coefficient cp - (w - cc - 1).
+//
+// Returns the number of pivots k, or -1 in forced mode when a given pivot
+// vanished.  Unless forced mode, k == w or keep != 0, E is not needed and is
+// not formed; otherwise Et[u * NB + t] = balanced E[t][u] for t, u < k
+// rounded up to 4, zero padded.  Fills sm.J, sm.Pi, sm.own (search).
+template <int NB>
+__device__ int bt_window_gj(const uint32_t* __restrict__ A, int64_t ld, int r, int c0, int w, int rows,
+                            int forced, int keep, const Field& f, uint32_t* G, unsigned char* isp,
+                            BtSmall<NB>& sm, int32_t* Et) {
+    constexpr int SWG = 2 * NB + 1;
+    constexpr int CW = NB;                  // column slots
+    constexpr int RGN = BT_THREADS / CW;    // row groups
+    constexpr int UMAX = (bt_win_rows(NB) + RGN - 1) / RGN;
+    constexpr int U = UMAX < 4 ? UMAX : 4;  // rows per batch of independent updates
+    static_assert(BT_THREADS % CW == 0, "column slots must divide the block");
+    const int tid = threadIdx.x;
+    const int cp = tid % CW, rg = tid / CW;
+    uint32_t* sig = G + bt_win_rows(NB) * SWG;
+    uint32_t* hd = sig + bt_win_rows(NB);
+    int cand = INT_MAX;
+    for (int e = tid; e < rows * 2 * NB; e += BT_THREADS) {
+        const int i = e / (2 * NB), c = e % (2 * NB);
+        const int64_t arow = forced ? (int64_t)sm.Pi[i] : (int64_t)(r + i);
+        const uint32_t v = c < w ? A[arow * ld + c0 + c] : 0u;
+        G[i * SWG + c] = v;
+        if (c == 0) {
+            sig[i] = 1u;
+            hd[i] = 0u;
+            isp[i] = 0;
+            if (v != 0u && i < cand) cand = i;
+        }
+    }
+    int buf = 0;
+    int q = INT_MAX;
+    if (forced) __syncthreads();
+    else q = block_min1<NB>(cand, sm, buf);   // also the barrier after the load
+    int s = 0;
+    for (int cc = 0; cc < w; ++cc) {
+        int qq = -1;   // window row of this column's pivot
+        if (forced) {
+            if (s < rows && sm.J[s] - c0 == cc) qq = s;
+            else continue;   // not a pivot column of the pattern: nothing changes
+        } else if (q != INT_MAX) {
+            qq = q;
+        }
+        const bool has = qq >= 0;
+        uint32_t h = 0u, sq = 0u;
+        if (has) {
+            h = G[qq * SWG + cc];
+            sq = sig[qq];
+            if (h == 0u) return -1;   // forced mode only (a found pivot is nonzero); uniform
+            if (!forced && tid == 0) {
+                isp[qq] = 1;
+                sm.J[s] = c0 + cc;
+                sm.Pi[s] = r + qq;
+                sm.own[s] = qq;
+            }
+        }
+        const int np = w - cc - 1;
+        int col = -1;
+        if (cp < np) col = cc + 1 + cp;
+        else if (has && cp - np <= s) col = NB + (cp - np);
+        const bool act = has && col >= 0;
+        const bool col_s = has && col == NB + s;
+        const uint32_t pv = col_s ? sq : (act ? G[qq * SWG + col] : 0u);
+        const bool cand_col = !forced && cp == 0 && np > 0;   // col == cc + 1
+        cand = INT_MAX;
+        if (act || cand_col) {
+            for (int i0 = rg; i0 < rows; i0 += U * RGN) {
+                uint32_t x[U], fi[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * RGN;
+                    const bool ok = i < rows && i != qq;
+                    fi[u] = (ok && has) ? G[i * SWG + cc] : 0u;
+                    x[u] = ok ? G[i * SWG + col] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * RGN;
+                    if (act && fi[u] != 0u) {
+                        x[u] = mul2add(h, x[u], f.p - fi[u], pv, f);
+                        G[i * SWG + col] = x[u];
+                        if (col_s) {
+                            const bool prow = forced ? i < s : isp[i] != 0;
+                            if (prow) hd[i] = mulmod(h, hd[i], f);
+                            else sig[i] = mulmod(h, sig[i], f);
+                        }
+                    }
+                    if (cand_col && x[u] != 0u && i < rows && i != qq && !isp[i] && i < cand) cand = i;
+                }
+            }
+        }
+        if (col_s && qq % RGN == rg) {
+            G[qq * SWG + col] = sq;
+            hd[qq] = h;
+        }
+        if (has) ++s;
+        if (!forced && cc + 1 < w) q = block_min1<NB>(cand, sm, buf);
+        else __syncthreads();
+    }
+    const int k = s;
+    if (!forced && k < w && !keep) return k;
+    for (int t = tid; t < k; t += BT_THREADS) sm.hinv[t] = inverse_fermat(hd[forced ? t : sm.own[t]], f);
+    __syncthreads();
+    const int kp = (k + 3) & ~3;
+    for (int e = tid; e < kp * kp; e += BT_THREADS) {
+        const int u = e / kp, t = e % kp;
+        int32_t v = 0;
+        if (t < k && u < k) v = to_balanced(mulmod(G[(forced ? t : sm.own[t]) * SWG + NB + u], sm.hinv[t], f), f);
+        Et[u * NB + t] = v;
+    }
+    __syncthreads();
+    return k;
+}
 
 // Reduce system A (m x n, leading dimension ld) in place.  mode 0: pivot
 // search; mode 1: reuse the probe's pattern (pat_J / pat_Pi / pat_k per
@@ -186,64 +350,69 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
     for (int c0 = 0; c0 < ns && r < m; c0 += NB, ++panel) {
         const int w = min(NB, ns - c0);
         int k = 0;
+        bool e_ready = true;
         if (mode == 0) {
-          // The pivots of a panel come from a window of the first w + 32
-          // remaining rows: the RREF does not depend on which rows supply the
-          // pivots, so if the window already yields one pivot per panel column
-          // the pivot columns are settled; otherwise the panel is redone over
-          // all remaining rows.
-          const int rows_all = m - r;
-          for (int rows = min(rows_all, w + 32);; rows = rows_all) {
-            k = 0;
-            for (int e = tid; e < rows * w; e += BT_THREADS) {
-                const int i = e / w, j = e % w;
-                P[i * SW + j] = A[(int64_t)(r + i) * ld + c0 + j];
-            }
-            for (int i = tid; i < rows; i += BT_THREADS) isp[i] = 0;
-            __syncthreads();
-            // candidate for the first column
-            int cand = INT_MAX;
-            for (int i = tid; i < rows; i += BT_THREADS)
-                if (P[i * SW] != 0) { cand = i; break; }
-            int q = block_min<NB>(cand, sm);
-            for (int cc = 0; cc < w; ++cc) {
-                // q: lowest non-pivot row with a nonzero entry in column cc
-                if (q != INT_MAX) {
-                    if (tid == 0) {
-                        isp[q] = 1;
-                        sm.J[k] = c0 + cc;
-                        sm.Pi[k] = r + q;
-                        sm.own[k] = q;
-                    }
-                    ++k;
+            // Pivots from a window of the first w + BT_WINDOW remaining rows,
+            // with E from the same Gauss-Jordan pass.  The RREF does not depend
+            // on which rows supply the pivots, so the window's choice stands
+            // when it has a pivot in every panel column or holds every
+            // remaining row; otherwise the search covers all remaining rows
+            // with the fraction-free panel elimination, and E follows from its
+            // record.
+            const int rows_all = m - r;
+            const int wrows = min(rows_all, w + BT_WINDOW);
+            k = bt_window_gj<NB>(A, ld, r, c0, w, wrows, 0, wrows == rows_all, f, P, isp, sm, Et);
+            e_ready = k == w || wrows == rows_all;
+            if (!e_ready) {
+                const int rows = rows_all;
+                k = 0;
+                for (int e = tid; e < rows * w; e += BT_THREADS) {
+                    const int i = e / w, j = e % w;
+                    P[i * SW + j] = A[(int64_t)(r + i) * ld + c0 + j];
                 }
-                // eliminate column cc (fraction-free) and look for the next
-                // column's candidate in the same pass over the rows
-                cand = INT_MAX;
-                const uint32_t h = q != INT_MAX ? P[q * SW + cc] : 0u;
-                for (int i = warp; i < rows; i += NW) {
-                    if (i == q || isp[i]) continue;
-                    uint32_t* row = P + i * SW;
+                for (int i = tid; i < rows; i += BT_THREADS) isp[i] = 0;
+                __syncthreads();
+                // candidate for the first column
+                int cand = INT_MAX;
+                for (int i = tid; i < rows; i += BT_THREADS)
+                    if (P[i * SW] != 0) { cand = i; break; }
+                int q = block_min<NB>(cand, sm);
+                for (int cc = 0; cc < w; ++cc) {
+                    // q: lowest non-pivot row with a nonzero entry in column cc
                     if (q != INT_MAX) {
-                        const uint32_t fi = row[cc];
-                        if (fi != 0) {
-                            const uint32_t nf = f.p - fi;
-                            for (int j = cc + 1 + lane; j < w; j += 32)
-                                row[j] = mul2add(h, row[j], nf, P[q * SW + j], f);
+                        if (tid == 0) {
+                            isp[q] = 1;
+                            sm.J[k] = c0 + cc;
+                            sm.Pi[k] = r + q;
+                            sm.own[k] = q;
                         }
-                        __syncwarp();
+                        ++k;
                     }
-                    if (cc + 1 < w && lane == 0 && row[cc + 1] != 0 && i < cand) cand = i;
+                    // eliminate column cc (fraction-free) and look for the next
+                    // column's candidate in the same pass over the rows
+                    cand = INT_MAX;
+                    const uint32_t h = q != INT_MAX ? P[q * SW + cc] : 0u;
+                    for (int i = warp; i < rows; i += NW) {
+                        if (i == q || isp[i]) continue;
+                        uint32_t* row = P + i * SW;
+                        if (q != INT_MAX) {
+                            const uint32_t fi = row[cc];
+                            if (fi != 0) {
+                                const uint32_t nf = f.p - fi;
+                                for (int j = cc + 1 + lane; j < w; j += 32)
+                                    row[j] = mul2add(h, row[j], nf, P[q * SW + j], f);
+                            }
+                            __syncwarp();
+                        }
+                        if (cc + 1 < w && lane == 0 && row[cc + 1] != 0 && i < cand) cand = i;
+                    }
+                    if (cc + 1 < w) q = block_min<NB>(cand, sm);
+                    else __syncthreads();
                 }
-                if (cc + 1 < w) q = block_min<NB>(cand, sm);
-                else __syncthreads();
-            }
-            if (k == w || rows == rows_all) break;
-            __syncthreads();
-          }
-            for (int e = tid; e < k * w; e += BT_THREADS) {
-                const int t = e / w, j = e % w;
-                PU[t * NB + j] = P[sm.own[t] * SW + j];
+                for (int e = tid; e < k * w; e += BT_THREADS) {
+                    const int t = e / w, j = e % w;
+                    PU[t * NB + j] = P[sm.own[t] * SW + j];
+                }
             }
             if (rec_k && tid == 0) {
                 rec_k[panel] = k;
@@ -252,11 +421,10 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
                     rec_Pi[panel * NB + t] = sm.Pi[t];
                 }
             }
-            __syncthreads();   // P is dead from here on (F and the tiles reuse it)
+            __syncthreads();   // the slab is dead from here on (F and the tiles reuse it)
         } else {
-            // shared pattern: pivot rows and columns of the probe; eliminate the
-            // k pivot rows among themselves (the same recurrence the search
-            // would have applied to them)
+            // shared pattern: the probe's pivot rows and columns, eliminated in
+            // their order (the steps the search would have taken on them)
             k = pat_k[panel];
             for (int t = tid; t < k; t += BT_THREADS) {
                 sm.J[t] = pat_J[panel * NB + t];
@@ -264,26 +432,7 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
             }
             if (tid == 0) sm.s_fail = 0;
             __syncthreads();
-            for (int e = tid; e < k * w; e += BT_THREADS) {
-                const int t = e / w, j = e % w;
-                PU[t * NB + j] = A[(int64_t)sm.Pi[t] * ld + c0 + j];
-            }
-            __syncthreads();
-            for (int s = 0; s < k; ++s) {
-                const int cs = sm.J[s] - c0;
-                const uint32_t h = PU[s * NB + cs];
-                if (h == 0) { if (tid == 0) sm.s_fail = 1; }
-                for (int t = s + 1 + warp; t < k; t += NW) {
-                    uint32_t* row = PU + t * NB;
-                    const uint32_t fi = row[cs];
-                    if (fi == 0 || h == 0) continue;
-                    const uint32_t nf = f.p - fi;
-                    for (int j = cs + 1 + lane; j < w; j += 32)
-                        row[j] = mul2add(h, row[j], nf, PU[s * NB + j], f);
-                }
-                __syncthreads();
-            }
-            if (sm.s_fail) return false;
+            if (bt_window_gj<NB>(A, ld, r, c0, w, k, 1, 1, f, P, isp, sm, Et) < 0) return false;
         }
         if (k == 0) continue;
         // multipliers F (original entries at the pivot columns); loads unrolled
@@ -293,11 +442,13 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
             const int t = e / m, i = e - t * m;
             Ft[t * ldF + i] = to_balanced(A[(int64_t)i * ld + sm.J[t]], f);
         }
-        for (int t = tid; t < k; t += BT_THREADS) {
-            sm.hs[t] = PU[t * NB + (sm.J[t] - c0)];
-            sm.hinv[t] = inverse_mod(sm.hs[t], f.p);
+        if (!e_ready) {
+            for (int t = tid; t < k; t += BT_THREADS) {
+                sm.hs[t] = PU[t * NB + (sm.J[t] - c0)];
+                sm.hinv[t] = inverse_mod(sm.hs[t], f.p);
+            }
+            for (int e = tid; e < k * k; e += BT_THREADS) E[(e / k) * NB + (e % k)] = (e / k == e % k) ? 1u : 0u;
         }
-        for (int e = tid; e < k * k; e += BT_THREADS) E[(e / k) * NB + (e % k)] = (e / k == e % k) ? 1u : 0u;
         if (tid == 0) {
             // move plan: rows of [r, r+k) without a pivot go to the pivot rows' old places
             unsigned char occ[NB];
@@ -312,30 +463,32 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
             sm.s_npairs = a;
         }
         __syncthreads();
-        // E <- forward fraction-free recurrence, scaling, back substitution
-        for (int s = 0; s + 1 < k; ++s) {
-            const uint32_t h = sm.hs[s];
-            const int cs = sm.J[s] - c0;
-            for (int e = tid; e < (k - 1 - s) * k; e += BT_THREADS) {
-                const int t = s + 1 + e / k, j = e % k;
-                const uint32_t fts = PU[t * NB + cs];
-                if (fts) E[t * NB + j] = mul2add(h, E[t * NB + j], f.p - fts, E[s * NB + j], f);
+        if (!e_ready) {
+            // E <- forward fraction-free recurrence, scaling, back substitution
+            for (int s = 0; s + 1 < k; ++s) {
+                const uint32_t h = sm.hs[s];
+                const int cs = sm.J[s] - c0;
+                for (int e = tid; e < (k - 1 - s) * k; e += BT_THREADS) {
+                    const int t = s + 1 + e / k, j = e % k;
+                    const uint32_t fts = PU[t * NB + cs];
+                    if (fts) E[t * NB + j] = mul2add(h, E[t * NB + j], f.p - fts, E[s * NB + j], f);
+                }
+                __syncthreads();
             }
-            __syncthreads();
-        }
-        for (int e = tid; e < k * k; e += BT_THREADS) {
-            const int t = e / k, j = e % k;
-            E[t * NB + j] = mulmod(E[t * NB + j], sm.hinv[t], f);
-        }
-        __syncthreads();
-        for (int s = k - 1; s >= 1; --s) {
-            const int cs = sm.J[s] - c0;
-            for (int e = tid; e < s * k; e += BT_THREADS) {
+            for (int e = tid; e < k * k; e += BT_THREADS) {
                 const int t = e / k, j = e % k;
-                const uint32_t c = mulmod(PU[t * NB + cs], sm.hinv[t], f);
-                if (c) E[t * NB + j] = mul2add(1u, E[t * NB + j], f.p - c, E[s * NB + j], f);
+                E[t * NB + j] = mulmod(E[t * NB + j], sm.hinv[t], f);
             }
             __syncthreads();
+            for (int s = k - 1; s >= 1; --s) {
+                const int cs = sm.J[s] - c0;
+                for (int e = tid; e < s * k; e += BT_THREADS) {
+                    const int t = e / k, j = e % k;
+                    const uint32_t c = mulmod(PU[t * NB + cs], sm.hinv[t], f);
+                    if (c) E[t * NB + j] = mul2add(1u, E[t * NB + j], f.p - c, E[s * NB + j], f);
+                }
+                __syncthreads();
+            }
         }
         const int npairs = sm.s_npairs;
         for (int e = tid; e < npairs * k; e += BT_THREADS) {
@@ -345,7 +498,7 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
         // E^T in balanced form (register-tiled R = E V reads 4 consecutive t);
         // kp = k rounded up to 4, with zero padding
         const int kp = (k + 3) & ~3;
-        {
+        if (!e_ready) {
             // transpose through registers: each thread owns whole (t, s) entries
             uint32_t v[NB * NB / BT_THREADS + 1];
             int cnt = 0;

@@ -131,6 +131,20 @@ __device__ __forceinline__ uint32_t inverse_mod(uint32_t a, uint32_t p) {
     return u == 1 ? x1 : x2;
 }
 
+// Modular inverse of a (0 < a < p, p prime) as a^(p-2) (Fermat's little
+// theorem), by left-to-right binary exponentiation.  The exponent is the same
+// for every thread, so a warp inverting many values never diverges.  Returns
+// 0 for a == 0.
+__device__ __forceinline__ uint32_t inverse_fermat(uint32_t a, const Field& f) {
+    const uint32_t e = f.p - 2u;
+    uint32_t x = a;
+    for (int b = 30 - __clz(e); b >= 0; --b) {
+        x = mulmod(x, x, f);
+        if ((e >> b) & 1u) x = mulmod(x, a, f);
+    }
+    return x;
+}
+
 // ---------------------------------------------------------------------------
 // Bounded spin limits.  Every wait on another block gives up after about
 // kSpinCycles clocks, records LINAC_ERR_TIMEOUT in the status word and lets
