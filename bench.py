@@ -399,72 +399,80 @@ def cpu_leg(args, pristine, m, n, p):
                       f"({macs:.3e} field MACs, {dt:.1f} s, {cores} threads)"}
 
 
-def batched_leg(args, linac, synth, dev, stream):
-    """10,000 uneven systems [A | B] (n log-uniform in [32, 512], 4 RHS, 10 %
-    rank-deficient), one linac_rref_batched call per step."""
+def _batched_graph(linac, B, dev, flags):
+    """Device copies of a packed batch, one eager call (creates the library's
+    scratch), then the call captured into a CUDA graph on a side stream (the
+    default stream cannot be captured).  Returns (graph, stream, data,
+    pristine data, outputs)."""
     import torch
-    B = synth.batched_uneven(count=args.batch_count)
-    widths = linac.linac_batched_tune(B.p)          # once per process, untimed
-    data0 = torch.from_numpy(B.data.view(np.int32)).to(dev)
-    data = torch.empty_like(data0)
-    offs = torch.from_numpy(B.offsets).to(dev)
-    mm = torch.from_numpy(B.m).to(dev)
-    nn = torch.from_numpy(B.n).to(dev)
-    ld = torch.from_numpy(B.ld).to(dev)
-    ns = torch.from_numpy(B.nA).to(dev)
+    stream = torch.cuda.Stream()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    data0 = t(B.data.view(np.int32))
+    offs, mm, nn, ld, ns = t(B.offsets), t(B.m), t(B.n), t(B.ld), t(B.nA)
+    max_m, max_n = int(B.m.max()), int(B.n.max())
+    with torch.cuda.stream(stream):
+        data = data0.clone()
+        outs = linac.batched_outputs(mm, nn, ns)
+        call = lambda: linac.linac_rref_batched_into(data, offs, mm, nn, ld, B.p, *outs, max_m=max_m,
+                                                     max_n=max_n, nsearch=ns, flags=flags)
+        call()
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        call()
+    return g, stream, data, data0, outs
+
+
+def _time_graph(g, data, data0, stream, reps):
+    """Median CUDA-event time of graph replays on restored inputs."""
+    import torch
     times = []
-    for it in range(4):
-        data.copy_(data0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ranks, piv, poff, st = linac.linac_rref_batched(data, offs, mm, nn, ld, B.p, nsearch=ns,
-                                                        max_m=int(B.m.max()), max_n=int(B.n.max()))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if it:
-            times.append(e0.elapsed_time(e1))
-    ms = statistics.median(times)
-    rk = ranks.cpu().numpy()
-    ok = bool((rk == B.nA - B.deficiency).all())
-    macs = sum((int(B.m[s]) - 1) * (int(B.n[s]) * int(rk[s]) - int(rk[s]) * (int(rk[s]) + 1) // 2)
-               for s in range(B.count))
-    return {"systems": B.count, "systems_per_s": B.count / (ms / 1000.0), "ms": ms, "panel_widths": widths,
-            "field_macs_per_s_approx": macs / (ms / 1000.0), "ranks_ok": ok,
-            "workload": "batched uneven [A|B], n log-uniform [32,512], 4 RHS, p = 2^31 - 19"}
-
-
-def shared_leg(args, linac, synth, dev, stream):
-    """4096 evaluations of a 384 x 400 block-banded polynomial template."""
-    import torch
-    B = synth.shared_pattern(count=4096)
-    widths = linac.linac_batched_tune(B.p)
-    data0 = torch.from_numpy(B.data.view(np.int32)).to(dev)
-    data = torch.empty_like(data0)
-    offs = torch.from_numpy(B.offsets).to(dev)
-    mm = torch.from_numpy(B.m).to(dev)
-    nn = torch.from_numpy(B.n).to(dev)
-    ld = torch.from_numpy(B.ld).to(dev)
-    ns = torch.from_numpy(B.nA).to(dev)
-    out = {}
-    for name, flags in (("search", 0), ("shared_pattern", linac.LINAC_SHARED_PATTERN)):
-        times = []
-        for it in range(3):
+    with torch.cuda.stream(stream):
+        for it in range(reps + 1):
             data.copy_(data0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ranks, piv, poff, st = linac.linac_rref_batched(data, offs, mm, nn, ld, B.p, nsearch=ns,
-                                                            flags=flags, max_m=384, max_n=400)
+            g.replay()
             e1.record(stream)
-            torch.cuda.synchronize()
+            stream.synchronize()
             if it:
                 times.append(e0.elapsed_time(e1))
-        ms = statistics.median(times)
+    return statistics.median(times)
+
+
+def batched_leg(args, linac, synth, dev, stream):
+    """10,000 uneven systems [A | B] (n log-uniform in [32, 512], 4 RHS, 10 %
+    rank-deficient): the whole linac_rref_batched call captured once into a
+    CUDA graph, one graph replay per step."""
+    B = synth.batched_uneven(count=args.batch_count)
+    widths = linac.linac_batched_tune(B.p)          # once per process, untimed
+    g, gs, data, data0, (ranks, piv, poff, st) = _batched_graph(linac, B, dev, 0)
+    ms = _time_graph(g, data, data0, gs, 3)
+    rk = ranks[:B.count].cpu().numpy()
+    ok = bool((rk == B.nA - B.deficiency).all())
+    macs = sum((int(B.m[s]) - 1) * (int(B.n[s]) * int(rk[s]) - int(rk[s]) * (int(rk[s]) + 1) // 2)
+               for s in range(B.count))
+    return {"systems": B.count, "systems_per_s": B.count / (ms / 1000.0), "ms": ms, "panel_widths": widths,
+            "field_macs_per_s_approx": macs / (ms / 1000.0), "ranks_ok": ok, "launch": "cuda_graph",
+            "workload": "batched uneven [A|B], n log-uniform [32,512], 4 RHS, p = 2^31 - 19"}
+
+
+def shared_leg(args, linac, synth, dev, stream):
+    """4096 evaluations of a 384 x 400 block-banded polynomial template, with
+    and without the shared pivot pattern (each call captured in a CUDA graph)."""
+    B = synth.shared_pattern(count=4096)
+    widths = linac.linac_batched_tune(B.p)
+    out = {}
+    for name, flags in (("search", 0), ("shared_pattern", linac.LINAC_SHARED_PATTERN)):
+        g, gs, data, data0, (ranks, piv, poff, st) = _batched_graph(linac, B, dev, flags)
+        ms = _time_graph(g, data, data0, gs, 2)
         out[name] = {"systems_per_s": B.count / (ms / 1000.0), "ms": ms,
-                     "ranks_ok": bool((ranks.cpu().numpy() == 384).all())}
+                     "ranks_ok": bool((ranks[:B.count].cpu().numpy() == 384).all())}
+        del g
     out["speedup"] = out["search"]["ms"] / out["shared_pattern"]["ms"]
     out["panel_widths"] = widths
+    out["launch"] = "cuda_graph"
     return out
 
 

@@ -206,7 +206,7 @@ struct BtFold {
 // not formed; otherwise Et[u * NB + t] = balanced E[t][u] for t, u < k
 // rounded up to 4, zero padded.  Fills sm.J, sm.Pi, sm.own (search).
 template <int NB>
-__device__ int bt_window_gj(const uint32_t* __restrict__ A, int64_t ld, int r, int c0, int w, int rows,
+__device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int64_t ld, int r, int c0, int w, int rows,
                             int forced, int keep, const Field& f, uint32_t* G, unsigned char* isp,
                             BtSmall<NB>& sm, int32_t* Et) {
     constexpr int SWG = 2 * NB + 1;
@@ -322,7 +322,7 @@ __device__ int bt_window_gj(const uint32_t* __restrict__ A, int64_t ld, int r, i
 // the result leaves echelon form.  Returns true on success; writes rank and
 // pivots.
 template <int NB>
-__device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, int ns, const Field& f,
+__device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, int ns, const Field& f,
                           const BtFold& fo, int32_t* __restrict__ piv, int* rank_out, uint8_t* smem,
                           const BtLayout& L, BtSmall<NB>& sm, int mode, const int32_t* pat_J,
                           const int32_t* pat_Pi, const int* pat_k, int32_t* rec_J, int32_t* rec_Pi, int* rec_k) {
@@ -668,28 +668,42 @@ __device__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, in
     return true;
 }
 
-// Persistent kernel over one bucket.  pass 0: the bucket's systems (search,
-// or the shared pattern); pass 1: systems that failed the pattern (search).
+// Panel width of each size bucket for one launch.
+struct BtWidths {
+    int nb[BT_NBUCKETS];
+};
+
+__host__ __device__ inline int bt_bucket_of(int m) {
+    int b = 0;
+    while (b + 1 < BT_NBUCKETS && m > bt_bucket_max(b)) ++b;
+    return b;
+}
+
+// Persistent kernel over the size buckets blo..bhi, which share the panel
+// width NB (one launch for all buckets of one width whose shared-memory needs
+// allow the same blocks per SM).  Blocks pull systems, largest first, from a
+// device work counter.  pass 0: the buckets' systems (search, or the shared
+// pattern); pass 1: systems that failed the pattern (search).
 template <int NB>
 __global__ void __launch_bounds__(BT_THREADS, NB >= 64 ? 1 : 2)
 batched_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ offsets, const int32_t* __restrict__ dm,
                const int32_t* __restrict__ dn, const int32_t* __restrict__ dld, const int32_t* __restrict__ dns,
-               const int32_t* __restrict__ order, int bucket, int mmax, Field f, int32_t* __restrict__ ranks,
+               const int32_t* __restrict__ order, int blo, int bhi, Field f, int32_t* __restrict__ ranks,
                int32_t* __restrict__ pivots, const int64_t* __restrict__ piv_off, int32_t* __restrict__ sys_status,
                BatchScratch* bs, int pass, int use_pattern, const int32_t* pat_J, const int32_t* pat_Pi,
                int32_t* fallback, BtFold fo) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ BtSmall<NB> sm;
-    const BtLayout L = bt_layout(mmax, NB);
+    const BtLayout L = bt_layout(bt_bucket_max(bhi), NB);   // sized for the group's largest systems
     int begin, end;
     if (pass == 0) {
-        begin = bs->bbeg[bucket];
-        end = bs->bend[bucket];
+        begin = bs->bbeg[bhi];
+        end = bs->bend[blo];
     } else {
         begin = 0;
         end = bs->nfallback;
     }
-    unsigned int* counter = &bs->counters[pass * BT_NBUCKETS + bucket];
+    unsigned int* counter = &bs->counters[pass * BT_NBUCKETS + blo];
     if (use_pattern && pass == 0 && !bs->pattern_ok) use_pattern = 0;
     for (;;) {
         if (threadIdx.x == 0) sm.s_sys = (int)atomicAdd(counter, 1u);
@@ -699,26 +713,27 @@ batched_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ offsets,
         if (idx >= end) return;
         const int s = pass == 0 ? order[idx] : fallback[idx];
         const int m = dm[s], n = dn[s];
-        if (pass == 1 && mmax < m) continue;           // fallback systems are split by bucket too
-        if (pass == 1 && bucket > 0 && m <= bt_bucket_max(bucket - 1)) continue;
+        if (pass == 1) {   // fallback systems are split by bucket too
+            const int b = bt_bucket_of(m);
+            if (b < blo || b > bhi) continue;
+        }
         const int ns = dns ? min(dns[s], n) : n;
         uint32_t* A = data + offsets[s];
         int32_t* piv = pivots + piv_off[s];
         int rank = 0;
-        bool ok;
+        bool ok = false;
         // the pattern applies only to systems shaped like the probe
         const bool same_shape = m == bs->probe_m && n == bs->probe_n && ns == bs->probe_ns;
-        if (use_pattern && pass == 0 && !same_shape) {
-            ok = false;
-            if (threadIdx.x == 0) fallback[atomicAdd(&bs->nfallback, 1)] = s;
-        } else if (use_pattern && pass == 0) {
+        const int mode = use_pattern && pass == 0 ? 1 : 0;
+        // two call sites so that each is specialised for its mode
+        if (mode == 1 && !same_shape) ok = false;
+        else if (mode == 1)
             ok = bt_reduce<NB>(A, m, n, dld[s], ns, f, fo, piv, &rank, smem, L, sm, 1, pat_J, pat_Pi,
                                bs->pattern_k, nullptr, nullptr, nullptr);
-            if (!ok && threadIdx.x == 0) fallback[atomicAdd(&bs->nfallback, 1)] = s;
-        } else {
+        else
             ok = bt_reduce<NB>(A, m, n, dld[s], ns, f, fo, piv, &rank, smem, L, sm, 0, nullptr, nullptr, nullptr,
                                nullptr, nullptr, nullptr);
-        }
+        if (mode == 1 && !ok && threadIdx.x == 0) fallback[atomicAdd(&bs->nfallback, 1)] = s;
         __syncthreads();
         if (ok && threadIdx.x == 0) {
             ranks[s] = rank;
@@ -800,46 +815,84 @@ void bt_set_bucket_nb(int b, int nb) {
     if (dev >= 0 && dev < 64 && b >= 0 && b < BT_NBUCKETS) g_bt_nb[dev][b] = nb;
 }
 
-template <int NB>
-static linac_status launch_bucket(int b, int pass, int use_pattern, uint32_t* d_data, const int64_t* d_offsets,
-                                  const int32_t* d_m, const int32_t* d_n, const int32_t* d_ld,
-                                  const int32_t* d_nsearch, const int32_t* order, const Field& f,
-                                  int32_t* d_ranks, int32_t* d_pivots, const int64_t* d_piv_offsets,
-                                  int32_t* d_status, BatchScratch* bs, const int32_t* pat_J,
-                                  const int32_t* pat_Pi, int32_t* fallback, cudaStream_t stream) {
-    const int mmax = bt_bucket_max(b);
-    const BtLayout L = bt_layout(mmax, NB);
-    LINAC_CUDA_TRY(cudaFuncSetAttribute(batched_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)L.total));
+// Blocks per SM of one launch over buckets blo..bhi with widths wd (0 when
+// the launch does not fit).
+static int bt_group_occupancy(int blo, int bhi, const BtWidths& wd, size_t* smem_out) {
+    size_t smem = 0;
+    for (int b = blo; b <= bhi; ++b) {
+        if (wd.nb[b] != wd.nb[blo]) return 0;   // one width per launch
+        smem = std::max(smem, bt_layout(bt_bucket_max(b), wd.nb[b]).total);
+    }
+    int max_smem = 0;
+    if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess) return 0;
+    if (smem + sizeof(BtSmall<64>) > (size_t)max_smem) return 0;
+    const void* fn = nullptr;
+    switch (wd.nb[blo]) {
+        case 16: fn = (const void*)batched_kernel<16>; break;
+        case 32: fn = (const void*)batched_kernel<32>; break;
+        case 64: fn = (const void*)batched_kernel<64>; break;
+        default: return 0;
+    }
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int occ = 0;
-    LINAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel<NB>, BT_THREADS, L.total));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BT_THREADS, smem) != cudaSuccess) return 0;
+    if (smem_out) *smem_out = smem;
+    return occ;
+}
+
+static linac_status launch_group(int blo, int bhi, int pass, int use_pattern, const BtWidths& wd,
+                                 uint32_t* d_data, const int64_t* d_offsets, const int32_t* d_m, const int32_t* d_n,
+                                 const int32_t* d_ld, const int32_t* d_nsearch, const int32_t* order,
+                                 const Field& f, int32_t* d_ranks, int32_t* d_pivots, const int64_t* d_piv_offsets,
+                                 int32_t* d_status, BatchScratch* bs, const int32_t* pat_J, const int32_t* pat_Pi,
+                                 int32_t* fallback, cudaStream_t stream) {
+    size_t smem = 0;
+    const int occ = bt_group_occupancy(blo, bhi, wd, &smem);
+    (void)cudaGetLastError();
     if (occ < 1) return LINAC_ERR_UNSUPPORTED;
     const int grid = occ * sm_count();
     ProfScope ps(stream, use_pattern ? PROF_PATTERN : PROF_BATCHED);
-    batched_kernel<NB><<<grid, BT_THREADS, L.total, stream>>>(d_data, d_offsets, d_m, d_n, d_ld, d_nsearch, order, b,
-                                                              mmax, f, d_ranks, d_pivots, d_piv_offsets, d_status, bs,
-                                                              pass, use_pattern, pat_J, pat_Pi, fallback,
-                                                              bt_fold_params(f));
+    switch (wd.nb[blo]) {
+#define LINAC_BT_LAUNCH(NBV)                                                                                         \
+    case NBV:                                                                                                        \
+        batched_kernel<NBV><<<grid, BT_THREADS, smem, stream>>>(d_data, d_offsets, d_m, d_n, d_ld, d_nsearch, order, \
+                                                                blo, bhi, f, d_ranks, d_pivots, d_piv_offsets,       \
+                                                                d_status, bs, pass, use_pattern, pat_J, pat_Pi,      \
+                                                                fallback, bt_fold_params(f));                        \
+        break;
+        LINAC_BT_LAUNCH(16)
+        LINAC_BT_LAUNCH(32)
+        LINAC_BT_LAUNCH(64)
+#undef LINAC_BT_LAUNCH
+        default: return LINAC_ERR_ARG;
+    }
     LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;
 }
 
-static linac_status launch_bucket_nb(int nb, int b, int pass, int use_pattern, uint32_t* d_data,
-                                     const int64_t* d_offsets, const int32_t* d_m, const int32_t* d_n,
-                                     const int32_t* d_ld, const int32_t* d_nsearch, const int32_t* order,
-                                     const Field& f, int32_t* d_ranks, int32_t* d_pivots,
-                                     const int64_t* d_piv_offsets, int32_t* d_status, BatchScratch* bs,
-                                     const int32_t* pat_J, const int32_t* pat_Pi, int32_t* fallback,
-                                     cudaStream_t stream) {
-#define LINAC_BT_ARGS b, pass, use_pattern, d_data, d_offsets, d_m, d_n, d_ld, d_nsearch, order, f, d_ranks, \
-                      d_pivots, d_piv_offsets, d_status, bs, pat_J, pat_Pi, fallback, stream
-    switch (nb) {
-        case 16: return launch_bucket<16>(LINAC_BT_ARGS);
-        case 32: return launch_bucket<32>(LINAC_BT_ARGS);
-        case 64: return launch_bucket<64>(LINAC_BT_ARGS);
-        default: return LINAC_ERR_ARG;
+// Launch groups for buckets 0..top: consecutive buckets of one panel width
+// share one launch as long as sharing keeps every one of them at its own
+// blocks per SM (a larger bucket whose shared memory would cost the smaller
+// ones occupancy gets a launch of its own).  Returns the number of groups; group g is
+// [lo[g], hi[g]].
+static int bt_groups(int top, const BtWidths& wd, int* lo, int* hi) {
+    int ng = 0;
+    for (int b = 0; b <= top; ++b) {
+        if (ng > 0) {
+            const int g = ng - 1;
+            const int occ_g = bt_group_occupancy(lo[g], hi[g], wd, nullptr);
+            const int occ_b = bt_group_occupancy(b, b, wd, nullptr);
+            const int occ_m = bt_group_occupancy(lo[g], b, wd, nullptr);
+            if (occ_m >= 1 && occ_m == occ_g && occ_m == occ_b) {
+                hi[g] = b;
+                continue;
+            }
+        }
+        lo[ng] = hi[ng] = b;
+        ++ng;
     }
-#undef LINAC_BT_ARGS
+    (void)cudaGetLastError();
+    return ng;
 }
 
 size_t bt_shared_bytes(int b, int nb) { return bt_layout(bt_bucket_max(b), nb).total; }
@@ -899,18 +952,21 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
         }
         LINAC_CUDA_TRY(cudaGetLastError());
     }
-    // every bucket uses the pattern's panel width when a pattern is shared
-    const int pat_nb = pattern ? bt_bucket_nb(top) : 0;
-    for (int b = top; b >= 0; --b) {
-        const int nb = pattern ? pat_nb : bt_bucket_nb(b);
-        s = launch_bucket_nb(nb, b, 0, pattern ? 1 : 0, d_data, d_offsets, d_m, d_n, d_ld, d_nsearch, order, f,
-                             d_ranks, d_pivots, d_piv_offsets, d_status, bs, pat_J, pat_Pi, fallback, stream);
-        if (s != LINAC_OK) return s;
+    // tuned widths; every bucket uses the pattern's panel width when a
+    // pattern is shared (pass 0)
+    BtWidths tuned, first;
+    for (int b = 0; b < BT_NBUCKETS; ++b) {
+        tuned.nb[b] = bt_bucket_nb(b);
+        first.nb[b] = pattern ? bt_bucket_nb(top) : tuned.nb[b];
     }
-    if (pattern) {
-        for (int b = top; b >= 0; --b) {
-            s = launch_bucket_nb(bt_bucket_nb(b), b, 1, 0, d_data, d_offsets, d_m, d_n, d_ld, d_nsearch, order, f,
-                                 d_ranks, d_pivots, d_piv_offsets, d_status, bs, pat_J, pat_Pi, fallback, stream);
+    for (int pass = 0; pass < (pattern ? 2 : 1); ++pass) {
+        const BtWidths& wd = pass == 0 ? first : tuned;
+        int glo[BT_NBUCKETS], ghi[BT_NBUCKETS];
+        const int ng = bt_groups(top, wd, glo, ghi);
+        for (int g = ng - 1; g >= 0; --g) {   // largest systems first
+            s = launch_group(glo[g], ghi[g], pass, pass == 0 && pattern ? 1 : 0, wd, d_data, d_offsets, d_m, d_n,
+                             d_ld, d_nsearch, order, f, d_ranks, d_pivots, d_piv_offsets, d_status, bs, pat_J,
+                             pat_Pi, fallback, stream);
             if (s != LINAC_OK) return s;
         }
     }

@@ -180,12 +180,10 @@ def linac_solve(A: torch.Tensor, B: torch.Tensor, p: int, *, path="auto", nb: in
     return X[:nA, :k], cons[:k].bool(), rank, piv[:min(m, nA)]
 
 
-def linac_rref_batched(data: torch.Tensor, offsets: torch.Tensor, m: torch.Tensor, n: torch.Tensor,
-                       ld: torch.Tensor, p: int, *, nsearch: torch.Tensor | None = None, flags: int = 0,
-                       max_m: int | None = None, max_n: int | None = None, stream=None):
-    """In-place RREF of a packed batch of systems (see include/linac.h).
-    Returns (ranks, pivots, piv_offsets, status) as CUDA tensors."""
-    dev = data.device
+def batched_outputs(m: torch.Tensor, n: torch.Tensor, nsearch: torch.Tensor | None = None):
+    """Output buffers of a packed batch: (ranks, pivots, piv_offsets, status),
+    with piv_offsets the exclusive prefix sum of min(m, nsearch or n)."""
+    dev = m.device
     batch = int(m.numel())
     mm = m.to(torch.int64)
     nn = (nsearch if nsearch is not None else n).to(torch.int64)
@@ -197,15 +195,38 @@ def linac_rref_batched(data: torch.Tensor, offsets: torch.Tensor, m: torch.Tenso
     pivots = torch.full((max(total, 1),), -1, dtype=torch.int32, device=dev)
     ranks = torch.zeros(max(batch, 1), dtype=torch.int32, device=dev)
     status = torch.zeros(max(batch, 1), dtype=torch.int32, device=dev)
+    return ranks, pivots, piv_off, status
+
+
+def linac_rref_batched_into(data: torch.Tensor, offsets: torch.Tensor, m: torch.Tensor, n: torch.Tensor,
+                            ld: torch.Tensor, p: int, ranks: torch.Tensor, pivots: torch.Tensor,
+                            piv_off: torch.Tensor, status: torch.Tensor | None, *, max_m: int, max_n: int,
+                            nsearch: torch.Tensor | None = None, flags: int = 0, stream=None):
+    """linac_rref_batched into caller-made outputs (see batched_outputs).
+    Argument marshalling only -- no allocation and no host synchronisation --
+    so the call can be captured into a CUDA graph once the library's scratch
+    for this stream exists (one uncaptured call of the same batch first)."""
+    _check(lib().linac_rref_batched(data.data_ptr(), offsets.data_ptr(), m.data_ptr(), n.data_ptr(),
+                                    ld.data_ptr(), nsearch.data_ptr() if nsearch is not None else None,
+                                    int(m.numel()), int(max_m), int(max_n), p, flags, ranks.data_ptr(),
+                                    pivots.data_ptr(), piv_off.data_ptr(),
+                                    status.data_ptr() if status is not None else None,
+                                    _stream_ptr(stream)), "linac_rref_batched")
+
+
+def linac_rref_batched(data: torch.Tensor, offsets: torch.Tensor, m: torch.Tensor, n: torch.Tensor,
+                       ld: torch.Tensor, p: int, *, nsearch: torch.Tensor | None = None, flags: int = 0,
+                       max_m: int | None = None, max_n: int | None = None, stream=None):
+    """In-place RREF of a packed batch of systems (see include/linac.h).
+    Returns (ranks, pivots, piv_offsets, status) as CUDA tensors."""
+    batch = int(m.numel())
+    ranks, pivots, piv_off, status = batched_outputs(m, n, nsearch)
     if max_m is None:
         max_m = int(m.max().item()) if batch else 0
     if max_n is None:
         max_n = int(n.max().item()) if batch else 0
-    _check(lib().linac_rref_batched(data.data_ptr(), offsets.data_ptr(), m.data_ptr(), n.data_ptr(),
-                                    ld.data_ptr(), nsearch.data_ptr() if nsearch is not None else None,
-                                    batch, int(max_m), int(max_n), p, flags, ranks.data_ptr(),
-                                    pivots.data_ptr(), piv_off.data_ptr(), status.data_ptr(),
-                                    _stream_ptr(stream)), "linac_rref_batched")
+    linac_rref_batched_into(data, offsets, m, n, ld, p, ranks, pivots, piv_off, status, max_m=max_m,
+                            max_n=max_n, nsearch=nsearch, flags=flags, stream=stream)
     return ranks[:batch], pivots, piv_off, status[:batch]
 
 
