@@ -57,6 +57,10 @@ def _load():
         lib.oracle_solve.restype = ctypes.c_int
         lib.oracle_inverse.argtypes = [u32, u32]
         lib.oracle_inverse.restype = u32
+        lib.oracle_load_matrix.argtypes = [vp, i64, i64, i64, vp, i64, i64, u32, vp, i64]
+        lib.oracle_load_matrix.restype = ctypes.c_int
+        lib.oracle_matmul.argtypes = [vp, i64, i64, i64, vp, i64, i64, u32, vp, i64]
+        lib.oracle_matmul.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -144,3 +148,73 @@ def null_space(R: np.ndarray, pivots: np.ndarray, p: int) -> np.ndarray:
         for t, c in enumerate(piv):
             K[c, f_idx] = R[t, f]
     return K.astype(np.uint32)
+
+
+def rank_factor(A, pivots) -> np.ndarray:
+    """C = A[:, J], the pivot columns of the ORIGINAL matrix (paper section
+    5.1): with R the RREF without its zero rows, A = C R is a rank
+    factorisation."""
+    A = _as_matrix(A)
+    J = np.asarray(pivots, dtype=np.int64)
+    return np.ascontiguousarray(A[:, J])
+
+
+def load_matrix(bases, lindices, p: int) -> np.ndarray:
+    """A[r][c] = prod_t bases[r][lindices[c][t]] mod p (paper sections 2.3 and
+    3.3: rows are sampling points, columns monomials)."""
+    bases = _as_matrix(bases)
+    L = np.ascontiguousarray(np.asarray(lindices, dtype=np.int32))
+    if L.ndim != 2:
+        raise ValueError("lindices must be n_cols x d")
+    n_rows, n_basis = bases.shape
+    n_cols, d = L.shape
+    A = np.zeros((n_rows, max(n_cols, 1)), dtype=np.uint32)
+    rc = _load().oracle_load_matrix(bases.ctypes.data, n_rows, n_basis, n_basis, L.ctypes.data,
+                                    n_cols, d, p, A.ctypes.data, A.shape[1])
+    if rc != 0:
+        raise ValueError("oracle_load_matrix rejected its arguments")
+    return A[:, :n_cols].copy()
+
+
+def matmul(A, B, p: int) -> np.ndarray:
+    """A B mod p, every product reduced before it is added."""
+    A = _as_matrix(A)
+    B = _as_matrix(B)
+    m, K = A.shape
+    if B.shape[0] != K:
+        raise ValueError("inner dimensions differ")
+    n = B.shape[1]
+    C = np.zeros((m, max(n, 1)), dtype=np.uint32)
+    rc = _load().oracle_matmul(A.ctypes.data, m, K, K, B.ctypes.data, n, n, p, C.ctypes.data, C.shape[1])
+    if rc != 0:
+        raise ValueError("oracle_matmul rejected its arguments")
+    return C[:, :n].copy()
+
+
+def eval_template(points, coefs, monomials, mask, p: int) -> np.ndarray:
+    """Evaluate a template of polynomial entries at many points (paper
+    section 3.3: a system is built by evaluating the same monomials at
+    different numerical points).
+
+    points: count x nv residues (one row per point); monomials: list of
+    exponent tuples, one per monomial; coefs: nnz x n_monomials coefficients
+    of the template's nonzero entries, in row-major order of the boolean
+    mask (rows x cols).  Each monomial's value at a point is a load_matrix
+    product of the point's variables (exponents unrolled into repeated
+    indices, padded with the constant 1); entry values are the monomial
+    values times the coefficients, summed mod p.  Returns count x rows x cols.
+    """
+    pts = _as_matrix(points)
+    count, nv = pts.shape
+    bases = np.concatenate([np.ones((count, 1), dtype=np.uint32), pts], axis=1)
+    deg = max(sum(e) for e in monomials)
+    lind = np.zeros((len(monomials), max(deg, 1)), dtype=np.int32)
+    for u, e in enumerate(monomials):
+        idx = [1 + v for v in range(nv) for _ in range(e[v])]
+        lind[u, :len(idx)] = idx
+    V = load_matrix(bases, lind, p)                               # count x n_monomials
+    vals = matmul(V, np.ascontiguousarray(np.asarray(coefs, dtype=np.uint32).T), p)   # count x nnz
+    mask = np.asarray(mask, dtype=bool)
+    out = np.zeros((count,) + mask.shape, dtype=np.uint32)
+    out[:, mask] = vals
+    return out

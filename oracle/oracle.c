@@ -226,3 +226,52 @@ int oracle_solve(uint32_t *M, int64_t m, int64_t nA, int64_t k, int64_t ld,
     }
     return 0;
 }
+
+/*
+ * Matrix construction of paper section 3.3 ("Building linear systems on
+ * GPUs") and section 2.3 (cuda_load_matrix): each row r is one sampling
+ * point given by its basis-variable values bases[r][0..n_basis), each column
+ * c one monomial given by d indices into those values, and
+ *     A[r][c] = prod_{t < d} bases[r][lindices[c][t]]  mod p.
+ * The product is taken left to right, reducing after every factor.
+ * lindices is n_cols x d, row-major.  Returns -1 for an index out of range.
+ */
+int oracle_load_matrix(const uint32_t *bases, int64_t n_rows, int64_t n_basis, int64_t ldb,
+                       const int32_t *lindices, int64_t n_cols, int64_t d, uint32_t p,
+                       uint32_t *A, int64_t lda) {
+    if (n_rows < 0 || n_cols < 0 || d < 0 || ldb < n_basis || lda < n_cols || p < 2) return -1;
+    for (int64_t c = 0; c < n_cols; c++)
+        for (int64_t t = 0; t < d; t++)
+            if (lindices[c * d + t] < 0 || lindices[c * d + t] >= n_basis) return -1;
+    for (int64_t r = 0; r < n_rows; r++) {
+        for (int64_t c = 0; c < n_cols; c++) {
+            uint64_t v = 1 % p;
+            for (int64_t t = 0; t < d; t++)
+                v = (v * (uint64_t)bases[r * ldb + lindices[c * d + t]]) % p;
+            A[r * lda + c] = (uint32_t)v;
+        }
+    }
+    return 0;
+}
+
+/*
+ * Plain matrix product over Z/pZ: C = A B mod p, A m x K, B K x n, all
+ * row-major with canonical residues.  Each product is reduced before it is
+ * added (uint64 '%').  Used to state the paper's identities A = C R (rank
+ * factorisation, section 5.1) and A K = 0 (null space, section 5.1), and to
+ * expand a template of polynomial entries at many points (section 3.3).
+ */
+int oracle_matmul(const uint32_t *A, int64_t m, int64_t K, int64_t lda,
+                  const uint32_t *B, int64_t n, int64_t ldb, uint32_t p,
+                  uint32_t *C, int64_t ldc) {
+    if (m < 0 || K < 0 || n < 0 || lda < K || ldb < n || ldc < n || p < 2) return -1;
+    for (int64_t i = 0; i < m; i++) {
+        for (int64_t j = 0; j < n; j++) {
+            uint64_t s = 0;
+            for (int64_t k = 0; k < K; k++)
+                s = (s + ((uint64_t)A[i * lda + k] * (uint64_t)B[k * ldb + j]) % p) % p;
+            C[i * ldc + j] = (uint32_t)s;
+        }
+    }
+    return 0;
+}

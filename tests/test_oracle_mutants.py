@@ -28,10 +28,23 @@ MUTANTS = {
                                         "X[(int64_t)t * ldx + j] = M[t * ld + nA + j];"),
 }
 
+# planted slips in the construction and product routines, caught by the
+# construction pins
+CONSTRUCTION_MUTANTS = {
+    "load_matrix_index_not_looked_up": ("v = (v * (uint64_t)bases[r * ldb + lindices[c * d + t]]) % p;",
+                                        "v = (v * (uint64_t)bases[r * ldb + t % n_basis]) % p;"),
+    "load_matrix_last_factor_dropped": ("for (int64_t t = 0; t < d; t++)\n                v = (v",
+                                        "for (int64_t t = 1; t < d; t++)\n                v = (v"),
+    "matmul_transposed_operand": ("(uint64_t)B[k * ldb + j]) % p) % p;", "(uint64_t)B[j * ldb + k]) % p) % p;"),
+    "matmul_inner_loop_short": ("for (int64_t k = 0; k < K; k++)\n                s = (s",
+                                "for (int64_t k = 1; k < K; k++)\n                s = (s"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(CONSTRUCTION_MUTANTS))
 def test_pins_fail_on_mutant(name, tmp_path):
-    before, after = MUTANTS[name]
+    before, after = MUTANTS[name] if name in MUTANTS else CONSTRUCTION_MUTANTS[name]
+    pins = "test_oracle_pins.py" if name in MUTANTS else "test_oracle_construction.py"
     src = open(SRC).read()
     assert src.count(before) == 1, f"mutation site for {name} not found exactly once"
     mut = tmp_path / "oracle_mut.c"
@@ -41,6 +54,6 @@ def test_pins_fail_on_mutant(name, tmp_path):
                    check=True)
     env = dict(os.environ, ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
