@@ -52,6 +52,15 @@ SM_MAX_MHZ = 2070.0       # GB300 maximum SM clock
 # 4 schedulers x a 16-lane multiply pipe, two passes per wide multiply-add
 # (ncu: ~4 pipe cycles per 32-thread warp instruction on GB300)
 IMAD_WIDE_PER_SM_CLK = 32
+# DRAM bytes per output of update_plain_kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of the third panel of the
+# 8192 x 8448 elimination: 481.3 MB for 8192 x 8192 outputs; summary in
+# profiles/update_plain_rref_8192x8448.md), valid while the kernel's sources
+# hash to UPDATE_SRC_SHA; the traffic is reported as null otherwise
+UPDATE_BYTES_PER_OUTPUT = 481.3e6 / (8192 * 8192)
+UPDATE_SRC_SHA = "62e4e4d25e82826b"
+UPDATE_SRC = ["paper_2605_25863_gb300/csrc/update_plain.cu", "paper_2605_25863_gb300/csrc/linac_device.cuh",
+              "paper_2605_25863_gb300/csrc/update.cuh"]
 
 
 def parse():
@@ -68,6 +77,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU oracle, path comparison and batched legs")
     ap.add_argument("--batch-count", type=int, default=10000)
+    ap.add_argument("--only", choices=["all", "batched"], default="all",
+                    help="batched: run the batched workload alone (a profiling aid; prints its own line)")
+    ap.add_argument("--widths", default="",
+                    help="comma-separated panel widths per size bucket for the batched legs (default: autotune)")
     ap.add_argument("--measure-peaks", action="store_true",
                     help="print the measured integer pipe rates (roofline denominators) and exit")
     return ap.parse_args()
@@ -88,6 +101,22 @@ def update_work(m: int, n: int, pivots, nb: int) -> int:
         k = int(((piv >= c0) & (piv < c0 + nb)).sum())
         total += (m - k) * (n - c0) * k
     return total
+
+
+def update_src_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in UPDATE_SRC:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def update_outputs(m: int, n: int, nb: int) -> int:
+    """Outputs written by the trailing updates of one elimination: m rows x
+    (n - c0) columns per panel start c0 (a panel without pivots launches no
+    update; the bench matrix has full rank)."""
+    return sum(m * (n - c0) for c0 in range(0, min(m, n), nb))
 
 
 def workload_name(m, n, rhs):
@@ -237,6 +266,9 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
+    if args.only == "batched":
+        print(json.dumps({"batched": batched_leg(args, linac, synth, dev, stream)}), flush=True)
+        return 0
 
     m, rhs = args.m, args.rhs
     n = m + rhs
@@ -269,7 +301,9 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("bench_timed")     # ncu --nvtx --nvtx-include "bench_timed/"
     events = [step() for _ in range(args.steps)]
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     if world > 1:
@@ -299,6 +333,9 @@ def run_ours(args):
     shift_fold = bin((1 << 32) % p).count("1") <= 3       # folds run on the ALU pipe
     imad_per_mac = 1.0 if shift_fold else 1.0 + 2.0 / fold
     achieved = upd_macs / (upd_ms / 1000.0) if upd_ms else 0.0
+    traffic = None
+    if upd_name == "update_plain" and upd_launches and update_src_sha() == UPDATE_SRC_SHA:
+        traffic = UPDATE_BYTES_PER_OUTPUT * update_outputs(m, n, nb) * args.steps / upd_launches
     peak = SMS * IMAD_WIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / imad_per_mac
     kernel_times = {k: {"launches": v[0], "total_ms": round(v[1], 3),
                         "share": round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4)}
@@ -314,7 +351,9 @@ def run_ours(args):
                          if m == 32768 else "input restored by a full device copy before every step"},
         "roofline": {"kernel": upd_name, "bound": "alu", "achieved": achieved / 1e12,
                      "peak": peak / 1e12, "unit": "Tfield-MAC/s", "frac": achieved / peak if peak else None,
-                     "traffic": None,
+                     "traffic": traffic,
+                     "traffic_basis": "ncu DRAM bytes per output of the 8192 x 8448 capture x outputs per launch"
+                                      if traffic is not None else "kernel changed since the ncu capture",
                      "peak_basis": f"{SMS} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x {SM_MAX_MHZ:.0f} MHz"
                                    f" / {imad_per_mac:.3f} per field MAC"
                                    f" ({'folds on the ALU pipe' if shift_fold else f'fold every {fold} on the multiply pipe'})",
@@ -333,6 +372,7 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_leg(args, pristine, m, n, p)
         line["batched"] = batched_leg(args, linac, synth, dev, stream)
         line["shared_pattern"] = shared_leg(args, linac, synth, dev, stream)
+        line["construction"] = construction_leg(args, linac, synth, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -441,12 +481,21 @@ def _time_graph(g, data, data0, stream, reps):
     return statistics.median(times)
 
 
+def batched_widths(args, linac, p):
+    """Panel widths per size bucket: --widths, else the autotuner (once per
+    process, untimed)."""
+    if args.widths:
+        linac.linac_batched_set_panel_widths([int(w) for w in args.widths.split(",")])
+        return linac.linac_batched_panel_widths()
+    return linac.linac_batched_tune(p)
+
+
 def batched_leg(args, linac, synth, dev, stream):
     """10,000 uneven systems [A | B] (n log-uniform in [32, 512], 4 RHS, 10 %
     rank-deficient): the whole linac_rref_batched call captured once into a
     CUDA graph, one graph replay per step."""
     B = synth.batched_uneven(count=args.batch_count)
-    widths = linac.linac_batched_tune(B.p)          # once per process, untimed
+    widths = batched_widths(args, linac, B.p)
     g, gs, data, data0, (ranks, piv, poff, st) = _batched_graph(linac, B, dev, 0)
     ms = _time_graph(g, data, data0, gs, 3)
     rk = ranks[:B.count].cpu().numpy()
@@ -462,7 +511,7 @@ def shared_leg(args, linac, synth, dev, stream):
     """4096 evaluations of a 384 x 400 block-banded polynomial template, with
     and without the shared pivot pattern (each call captured in a CUDA graph)."""
     B = synth.shared_pattern(count=4096)
-    widths = linac.linac_batched_tune(B.p)
+    widths = batched_widths(args, linac, B.p)
     out = {}
     for name, flags in (("search", 0), ("shared_pattern", linac.LINAC_SHARED_PATTERN)):
         g, gs, data, data0, (ranks, piv, poff, st) = _batched_graph(linac, B, dev, flags)
@@ -473,6 +522,104 @@ def shared_leg(args, linac, synth, dev, stream):
     out["speedup"] = out["search"]["ms"] / out["shared_pattern"]["ms"]
     out["panel_widths"] = widths
     out["launch"] = "cuda_graph"
+    return out
+
+
+def construction_leg(args, linac, synth, dev):
+    """Systems built on the device (paper section 3.3).
+
+    (a) linac_load_matrix at the paper's largest construction size, n = 20000
+        points x 20000 monomials of degree 8 over 64 basis variables (the
+        paper reports 2.6 s on an RTX 4070 Laptop GPU for n = 2 x 10^4).
+    (b) the shared-pattern workload end to end: monomial values of 4096 points
+        (load_matrix), the 384 x 400 template's coefficients applied to them
+        (linac_matmul), and the shared-pattern RREF of the 4096 systems, all
+        captured in one CUDA graph."""
+    import torch
+    out = {}
+    p = P31
+    # (a)
+    n, nb, d = 20000, 64, 8
+    bases = torch.from_numpy(synth.uniform((n, nb), p, synth.stream_key(20, "lm_bases")).view(np.int32)).to(dev)
+    g = np.random.default_rng(20)
+    lind = torch.from_numpy(g.integers(0, nb, size=(n, d), dtype=np.int64).astype(np.int32)).to(dev)
+    A = linac.padded(n, n, dev)
+    times = []
+    for it in range(4):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        linac.linac_load_matrix(bases, lind, p, out=A)
+        e1.record()
+        torch.cuda.synchronize()
+        if it:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    out["load_matrix"] = {"rows": n, "cols": n, "degree": d, "basis": nb, "ms": ms,
+                          "entries_per_s": n * n / (ms / 1e3), "modmul_per_s": n * n * d / (ms / 1e3),
+                          "write_gbs": n * n * 4 / (ms / 1e3) / 1e9, "paper_context": "2.6 s, RTX 4070 Laptop, n = 2e4"}
+    del A
+    # (b)
+    mask, coefs, mons = synth.shared_pattern_template()
+    count = 4096
+    rows, cols = mask.shape
+    pts = synth.uniform((count, 2), p, synth.stream_key(4, "sp_points"))
+    Cd = np.zeros((len(mons), rows * cols), dtype=np.uint32)
+    Cd[:, np.flatnonzero(mask.ravel())] = coefs.T
+    deg = max(a + b for a, b in mons)
+    li = np.zeros((len(mons), deg), dtype=np.int32)
+    for u, (a, b) in enumerate(mons):
+        idx = [1] * a + [2] * b
+        li[u, :len(idx)] = idx
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    bases2 = t(np.concatenate([np.ones((count, 1), dtype=np.uint32), pts], axis=1).view(np.int32))
+    lind2 = t(li)
+    Cdev = t(Cd.view(np.int32))
+    V = linac.padded(count, len(mons), dev)
+    data2 = linac.padded(count, rows * cols, dev)
+    flat = data2.view(-1)
+    offs = torch.arange(count, dtype=torch.int64, device=dev) * (rows * cols)
+    mm = torch.full((count,), rows, dtype=torch.int32, device=dev)
+    nn = torch.full((count,), cols, dtype=torch.int32, device=dev)
+    ns = torch.full((count,), cols - 16, dtype=torch.int32, device=dev)
+    s2 = torch.cuda.Stream()
+    with torch.cuda.stream(s2):
+        outs = linac.batched_outputs(mm, nn, ns)
+
+        def build_and_reduce():
+            linac.linac_load_matrix(bases2, lind2, p, out=V, stream=s2)
+            linac.linac_matmul(V, Cdev, p, out=data2, stream=s2)
+            linac.linac_rref_batched_into(flat, offs, mm, nn, nn, p, *outs, max_m=rows, max_n=cols, nsearch=ns,
+                                          flags=linac.LINAC_SHARED_PATTERN, stream=s2)
+        build_and_reduce()
+    s2.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s2):
+        build_and_reduce()
+    times, tb = [], []
+    with torch.cuda.stream(s2):
+        for it in range(4):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(s2)
+            graph.replay()
+            e1.record(s2)
+            # construction alone, eagerly, for its share
+            linac.linac_load_matrix(bases2, lind2, p, out=V, stream=s2)
+            linac.linac_matmul(V, Cdev, p, out=data2, stream=s2)
+            e2.record(s2)
+            s2.synchronize()
+            if it:
+                times.append(e0.elapsed_time(e1))
+                tb.append(e1.elapsed_time(e2))
+    ms2, msb = statistics.median(times), statistics.median(tb)
+    ranks = outs[0][:count].cpu().numpy()
+    out["template_pipeline"] = {
+        "systems": count, "ms": ms2, "systems_per_s": count / (ms2 / 1e3), "construction_ms": msb,
+        "construction_share": msb / ms2, "ranks_ok": bool((ranks == rows).all()), "launch": "cuda_graph",
+        "workload": "4096 evaluations of a 384 x 400 block-banded template of bivariate polynomials "
+                    "(degree <= 4, 16 RHS), built on the device and reduced with the shared pattern"}
     return out
 
 

@@ -198,6 +198,89 @@ linac_status linac_batched_tune(uint32_t p, int32_t *nb_out, cudaStream_t stream
 /* Current panel width per size bucket (5 entries). */
 linac_status linac_batched_panel_widths(int32_t *nb_out);
 
+/* Sets the panel width per size bucket for the current device (5 entries,
+ * each 16, 32 or 64, or 0 for the default 32), e.g. to reuse widths that
+ * linac_batched_tune chose in an earlier run.  Errors: LINAC_ERR_ARG (another
+ * value), LINAC_ERR_UNSUPPORTED (a width whose shared memory does not fit the
+ * device for that bucket); nothing is changed on error. */
+linac_status linac_batched_set_panel_widths(const int32_t *nb);
+
+/*
+ * linac_load_matrix -- build a linear system from monomials evaluated at
+ * sampling points (section 3.3, "Building linear systems on GPUs"; section
+ * 2.3, cuda_load_matrix):
+ *     A[r][c] = prod_{t < d} bases[r][lindices[c][t]]  mod p.
+ *   d_bases     n_rows x n_basis residues in [0, p), leading dimension
+ *               ld_bases: row r holds the basis-variable values of point r.
+ *   d_lindices  n_cols x d int32 indices into a row of bases (row-major,
+ *               contiguous): column c is the monomial whose factors they
+ *               name (pad lower-degree monomials with an index whose basis
+ *               value is 1, as the paper does).  d = 0 gives all ones.
+ *   d_A         n_rows x n_cols output, leading dimension ldA (any alignment).
+ * An index outside [0, n_basis) is not read: its entry is written as 0 and
+ * the device status word is set to LINAC_ERR_RANGE (linac_last_device_status).
+ * Errors: LINAC_ERR_ARG (negative sizes, ld too small, null pointers),
+ * LINAC_ERR_PRIME, LINAC_ERR_UNSUPPORTED (more than 524280 rows).
+ */
+linac_status linac_load_matrix(const uint32_t *d_bases, int64_t n_rows, int64_t n_basis, int64_t ld_bases,
+                               const int32_t *d_lindices, int64_t n_cols, int32_t d, uint32_t p,
+                               uint32_t *d_A, int64_t ldA, cudaStream_t stream);
+
+/*
+ * linac_matmul -- C = A B mod p for canonical residues: A is m x K (ldA),
+ * B is K x n (ldB), C is m x n (ldC), all row-major, any alignment.  Exact:
+ * the products of balanced residues accumulate in signed 64-bit registers
+ * with periodic folds, and every output is reduced once.  With the monomial
+ * values of many points as A and a template's coefficients as B, one call
+ * evaluates a template of polynomial entries at every point (section 3.3); it
+ * also states the identities A = C R and A K = 0 of section 5.1 on the device.
+ * Errors: LINAC_ERR_ARG, LINAC_ERR_PRIME, LINAC_ERR_UNSUPPORTED (m above
+ * 8388480).
+ */
+linac_status linac_matmul(const uint32_t *d_A, int64_t m, int64_t K, int64_t ldA,
+                          const uint32_t *d_B, int64_t n, int64_t ldB, uint32_t p,
+                          uint32_t *d_C, int64_t ldC, cudaStream_t stream);
+
+/*
+ * linac_null_space -- canonical basis of the null space read off an RREF
+ * (section 5.1): ker(A) = ker(R); the non-pivot columns are the free
+ * variables and their coefficients are fixed to minus the identity.
+ *   d_R, m, n, ld   the RREF (as linac_rref leaves it); d_rank, d_pivots its
+ *                   rank and pivot columns (device, as linac_rref writes them).
+ *   d_K             n x kcols output (leading dimension ldK): column q < the
+ *                   nullity n - rank belongs to the q-th free column f_q and
+ *                   holds p - 1 (that is, -1) in row f_q, R[t][f_q] in row
+ *                   pivots[t], and 0 elsewhere, so A K = 0; columns at or
+ *                   beyond the nullity are zero.
+ *   d_free          n int32: the free columns in increasing order, -1 after
+ *                   the nullity.
+ *   d_nullity       one int32: n - rank.
+ * Nothing is synchronised: kcols is the caller's bound on the nullity (n
+ * always suffices).  If the nullity exceeds kcols, the first kcols columns are
+ * written and the device status word is set to LINAC_ERR_RANGE.  Uses n * 4
+ * bytes of library scratch.
+ * Errors: LINAC_ERR_ARG, LINAC_ERR_PRIME, LINAC_ERR_NOMEM.
+ */
+linac_status linac_null_space(const uint32_t *d_R, int64_t m, int64_t n, int64_t ld,
+                              const int32_t *d_rank, const int32_t *d_pivots, uint32_t p,
+                              uint32_t *d_K, int64_t kcols, int64_t ldK, int32_t *d_free,
+                              int32_t *d_nullity, cudaStream_t stream);
+
+/*
+ * linac_rank_factor -- the left factor of the rank factorisation A = C R
+ * (section 5.1): C = A[:, J], the pivot columns J of the ORIGINAL matrix
+ * (keep a copy of A: linac_rref overwrites it), with R the RREF's first
+ * rank rows.
+ *   d_A, m, n, ld   the original matrix; d_rank, d_pivots from linac_rref.
+ *   d_C             m x ccols output (ldC): column t < rank is A's column
+ *                   pivots[t]; columns rank..ccols-1 are zero (ccols =
+ *                   min(m, n) always suffices).
+ * Errors: LINAC_ERR_ARG.
+ */
+linac_status linac_rank_factor(const uint32_t *d_A, int64_t m, int64_t n, int64_t ld,
+                               const int32_t *d_rank, const int32_t *d_pivots,
+                               uint32_t *d_C, int64_t ccols, int64_t ldC, cudaStream_t stream);
+
 /* Scratch bytes linac_rref_ex needs for an m x n problem with these options
  * (the library allocates them itself; exposed for capacity planning). */
 size_t linac_workspace_bytes(int64_t m, int64_t n, const linac_options *opts);

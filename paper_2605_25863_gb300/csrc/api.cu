@@ -70,6 +70,32 @@ Field make_field(uint32_t p) {
     return f;
 }
 
+int fold_shifts(const Field& f, FoldShifts* fs) {
+    uint32_t c = f.c32;
+    int n = 0;
+    fs->alu_reduce = 0;
+    fs->pad = 0;
+    for (int i = 0; i < 3; ++i) fs->e[i] = 0;
+    for (int b = 0; b < 32; ++b)
+        if ((c >> b) & 1u) {
+            if (n == 3) {
+                for (int i = 0; i < 3; ++i) fs->e[i] = 0;
+                n = 0;
+                break;
+            }
+            fs->e[n++] = (uint32_t)b;
+        }
+    for (int i = 0; i < 3; ++i) fs->s[i] = fs->e[i] == 0 ? 31u : 32u - fs->e[i];
+    if (n > 0) {
+        // bounds of reduce_alu (linac_device.cuh)
+        const unsigned __int128 cc = c;
+        const bool low_ok = cc * (cc + 1) / 2 <= f.p;
+        const bool high_ok = (((unsigned __int128)1) << 32) - 1 + cc * (cc / 2 + 1) < (unsigned __int128)3 * f.p;
+        fs->alu_reduce = low_ok && high_ok;
+    }
+    return n;
+}
+
 // ---------------------------------------------------------------------------
 // Scratch memory
 
@@ -262,6 +288,11 @@ linac_status linac_rref_batched(uint32_t* d_data, const int64_t* d_offsets, cons
 linac_status linac_batched_tune(uint32_t p, int32_t* nb_out, cudaStream_t stream) {
     if (!prime_ok(p)) return LINAC_ERR_PRIME;
     return batched_tune(make_field(p), nb_out, stream);
+}
+
+linac_status linac_batched_set_panel_widths(const int32_t* nb) {
+    if (!nb) return LINAC_ERR_ARG;
+    return batched_set_nb(nb);
 }
 
 linac_status linac_batched_panel_widths(int32_t* nb_out) {

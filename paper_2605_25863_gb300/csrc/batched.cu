@@ -162,21 +162,13 @@ __device__ __forceinline__ int block_min1(int v, BtSmall<NB>& sm, int& buf) {
     return x;
 }
 
-// Signed lazy accumulator fold: H*c32 + L, with H*c32 on the ALU pipe when
-// c32 = 2^32 mod p has at most three set bits (nshift > 0).
-__device__ __forceinline__ int64_t bt_fold(int64_t acc, const Field& f, int nshift, uint32_t e0, uint32_t e1,
-                                           uint32_t e2) {
-    if (nshift == 0) return fold64_fast(acc, f);
-    const int64_t h = acc >> 32;
-    int64_t r = (int64_t)(uint32_t)acc + (int64_t)((uint64_t)h << e0);
-    if (nshift > 1) r += (int64_t)((uint64_t)h << e1);
-    if (nshift > 2) r += (int64_t)((uint64_t)h << e2);
-    return r;
-}
-
+// Fold cadence of the lazy accumulators (fold after products t with
+// (t & mask) == mask) and the shift form of 2^32 mod p (fold_any,
+// reduce_acc in linac_device.cuh; nshift = 0 folds on the multiply pipe).
 struct BtFold {
-    int nshift, mask;   // fold after products t with (t & mask) == mask
-    uint32_t e0, e1, e2;
+    int mask;
+    int nshift;
+    FoldShifts fs;
 };
 
 // Pivots and E = G^{-1} of one panel from a window of rows, by fraction-free
@@ -321,7 +313,7 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
 // panel) and report failure (returns false) when a reused pivot vanishes or
 // the result leaves echelon form.  Returns true on success; writes rank and
 // pivots.
-template <int NB>
+template <int NB, int SH>
 __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n, int64_t ld, int ns, const Field& f,
                           const BtFold& fo, int32_t* __restrict__ piv, int* rank_out, uint8_t* smem,
                           const BtLayout& L, BtSmall<NB>& sm, int mode, const int32_t* pat_J,
@@ -548,13 +540,13 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
 #pragma unroll
                         for (int a = 0; a < 4; ++a)
 #pragma unroll
-                            for (int b = 0; b < 4; ++b) acc[a][b] = fold64_fast(acc[a][b], f);
+                            for (int b = 0; b < 4; ++b) acc[a][b] = fold_any<SH>(acc[a][b], f, fo.fs);
                     }
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) Rt[(t0 + a) * BT_TB + jq + b] = to_balanced(reduce_signed(acc[a][b], f), f);
+                    for (int b = 0; b < 4; ++b) Rt[(t0 + a) * BT_TB + jq + b] = to_balanced(reduce_acc<SH>(acc[a][b], f, fo.fs), f);
             }
             for (int e = tid; e < npairs * tw; e += BT_THREADS) {
                 const int a = e / tw, j = e % tw;
@@ -609,7 +601,7 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
 #pragma unroll
                         for (int a = 0; a < MR; ++a)
 #pragma unroll
-                            for (int b = 0; b < 4; ++b) acc[a][b] = fold64_fast(acc[a][b], f);
+                            for (int b = 0; b < 4; ++b) acc[a][b] = fold_any<SH>(acc[a][b], f, fo.fs);
                     }
                 }
 #pragma unroll
@@ -626,7 +618,7 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
                         uint32_t v = 0;
                         if (j < tw) {
                             if (prow) v = from_balanced(Rt[(d - r) * BT_TB + j], f);
-                            else v = submod(c4[b], reduce_signed(acc[a][b], f), f);
+                            else v = submod(c4[b], reduce_acc<SH>(acc[a][b], f, fo.fs), f);
                         }
                         o4[b] = v;
                         // shared pattern: rows below the new rank must vanish in the panel
@@ -684,7 +676,7 @@ __host__ __device__ inline int bt_bucket_of(int m) {
 // allow the same blocks per SM).  Blocks pull systems, largest first, from a
 // device work counter.  pass 0: the buckets' systems (search, or the shared
 // pattern); pass 1: systems that failed the pattern (search).
-template <int NB>
+template <int NB, int SH>
 __global__ void __launch_bounds__(BT_THREADS, NB >= 64 ? 1 : 2)
 batched_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ offsets, const int32_t* __restrict__ dm,
                const int32_t* __restrict__ dn, const int32_t* __restrict__ dld, const int32_t* __restrict__ dns,
@@ -728,10 +720,10 @@ batched_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ offsets,
         // two call sites so that each is specialised for its mode
         if (mode == 1 && !same_shape) ok = false;
         else if (mode == 1)
-            ok = bt_reduce<NB>(A, m, n, dld[s], ns, f, fo, piv, &rank, smem, L, sm, 1, pat_J, pat_Pi,
+            ok = bt_reduce<NB, SH>(A, m, n, dld[s], ns, f, fo, piv, &rank, smem, L, sm, 1, pat_J, pat_Pi,
                                bs->pattern_k, nullptr, nullptr, nullptr);
         else
-            ok = bt_reduce<NB>(A, m, n, dld[s], ns, f, fo, piv, &rank, smem, L, sm, 0, nullptr, nullptr, nullptr,
+            ok = bt_reduce<NB, SH>(A, m, n, dld[s], ns, f, fo, piv, &rank, smem, L, sm, 0, nullptr, nullptr, nullptr,
                                nullptr, nullptr, nullptr);
         if (mode == 1 && !ok && threadIdx.x == 0) fallback[atomicAdd(&bs->nfallback, 1)] = s;
         __syncthreads();
@@ -759,7 +751,7 @@ batched_probe_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ of
     for (int i = threadIdx.x; i < 1024 / 16 + 1; i += BT_THREADS) bs->pattern_k[i] = 0;
     __syncthreads();
     int rank = 0;
-    bt_reduce<NB>(data + offsets[0], m, n, dld[0], ns, f, fo, pivots + piv_off[0], &rank, smem, L, sm, 0, nullptr,
+    bt_reduce<NB, 0>(data + offsets[0], m, n, dld[0], ns, f, fo, pivots + piv_off[0], &rank, smem, L, sm, 0, nullptr,
                   nullptr, nullptr, pat_J, pat_Pi, bs->pattern_k);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -782,22 +774,29 @@ int g_bt_nb[64][BT_NBUCKETS];   // 0 = default
 
 static int bt_default_nb(int b) { (void)b; return 32; }
 
+// The shift form is used only when 2^32 mod p is a single power of two
+// (2^31 - 1): with two or three shifts the fold and the reduction issue more
+// ALU instructions than the multiply-pipe forms they replace, and this kernel
+// is bound by issue and latency rather than by the multiply pipe.
 static BtFold bt_fold_params(const Field& f) {
     BtFold fo;
     fo.mask = f.fold >= 8 ? 7 : 3;
-    uint32_t e[3] = {0, 0, 0};
-    int n = 0;
-    bool ok = true;
-    for (int b = 0; b < 32; ++b)
-        if ((f.c32 >> b) & 1u) {
-            if (n == 3) { ok = false; break; }
-            e[n++] = (uint32_t)b;
-        }
-    fo.nshift = ok ? n : 0;
-    fo.e0 = e[0];
-    fo.e1 = e[1];
-    fo.e2 = e[2];
+    fo.nshift = fold_shifts(f, &fo.fs);
+    if (fo.nshift != 1) {
+        fo.nshift = 0;
+        fo.fs.alu_reduce = 0;
+    }
     return fo;
+}
+
+// batched_kernel<nb, sh> (nullptr for an unsupported width).
+static const void* bt_kernel_fn(int nb, int sh) {
+    switch (nb) {
+        case 16: return sh == 1 ? (const void*)batched_kernel<16, 1> : (const void*)batched_kernel<16, 0>;
+        case 32: return sh == 1 ? (const void*)batched_kernel<32, 1> : (const void*)batched_kernel<32, 0>;
+        case 64: return sh == 1 ? (const void*)batched_kernel<64, 1> : (const void*)batched_kernel<64, 0>;
+        default: return nullptr;
+    }
 }
 
 int bt_bucket_nb(int b) {
@@ -817,7 +816,7 @@ void bt_set_bucket_nb(int b, int nb) {
 
 // Blocks per SM of one launch over buckets blo..bhi with widths wd (0 when
 // the launch does not fit).
-static int bt_group_occupancy(int blo, int bhi, const BtWidths& wd, size_t* smem_out) {
+static int bt_group_occupancy(int blo, int bhi, const BtWidths& wd, int sh, size_t* smem_out) {
     size_t smem = 0;
     for (int b = blo; b <= bhi; ++b) {
         if (wd.nb[b] != wd.nb[blo]) return 0;   // one width per launch
@@ -826,13 +825,8 @@ static int bt_group_occupancy(int blo, int bhi, const BtWidths& wd, size_t* smem
     int max_smem = 0;
     if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess) return 0;
     if (smem + sizeof(BtSmall<64>) > (size_t)max_smem) return 0;
-    const void* fn = nullptr;
-    switch (wd.nb[blo]) {
-        case 16: fn = (const void*)batched_kernel<16>; break;
-        case 32: fn = (const void*)batched_kernel<32>; break;
-        case 64: fn = (const void*)batched_kernel<64>; break;
-        default: return 0;
-    }
+    const void* fn = bt_kernel_fn(wd.nb[blo], sh);
+    if (!fn) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BT_THREADS, smem) != cudaSuccess) return 0;
@@ -847,26 +841,19 @@ static linac_status launch_group(int blo, int bhi, int pass, int use_pattern, co
                                  int32_t* d_status, BatchScratch* bs, const int32_t* pat_J, const int32_t* pat_Pi,
                                  int32_t* fallback, cudaStream_t stream) {
     size_t smem = 0;
-    const int occ = bt_group_occupancy(blo, bhi, wd, &smem);
+    BtFold fo = bt_fold_params(f);
+    const int occ = bt_group_occupancy(blo, bhi, wd, fo.nshift, &smem);
     (void)cudaGetLastError();
     if (occ < 1) return LINAC_ERR_UNSUPPORTED;
+    const void* fn = bt_kernel_fn(wd.nb[blo], fo.nshift);
+    if (!fn) return LINAC_ERR_ARG;
     const int grid = occ * sm_count();
+    Field fv = f;
+    void* args[] = {&d_data, (void*)&d_offsets, (void*)&d_m, (void*)&d_n, (void*)&d_ld, (void*)&d_nsearch,
+                    (void*)&order, &blo, &bhi, &fv, &d_ranks, &d_pivots, (void*)&d_piv_offsets, &d_status, &bs,
+                    &pass, &use_pattern, (void*)&pat_J, (void*)&pat_Pi, &fallback, &fo};
     ProfScope ps(stream, use_pattern ? PROF_PATTERN : PROF_BATCHED);
-    switch (wd.nb[blo]) {
-#define LINAC_BT_LAUNCH(NBV)                                                                                         \
-    case NBV:                                                                                                        \
-        batched_kernel<NBV><<<grid, BT_THREADS, smem, stream>>>(d_data, d_offsets, d_m, d_n, d_ld, d_nsearch, order, \
-                                                                blo, bhi, f, d_ranks, d_pivots, d_piv_offsets,       \
-                                                                d_status, bs, pass, use_pattern, pat_J, pat_Pi,      \
-                                                                fallback, bt_fold_params(f));                        \
-        break;
-        LINAC_BT_LAUNCH(16)
-        LINAC_BT_LAUNCH(32)
-        LINAC_BT_LAUNCH(64)
-#undef LINAC_BT_LAUNCH
-        default: return LINAC_ERR_ARG;
-    }
-    LINAC_CUDA_TRY(cudaGetLastError());
+    LINAC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(BT_THREADS), args, smem, stream));
     return LINAC_OK;
 }
 
@@ -875,14 +862,14 @@ static linac_status launch_group(int blo, int bhi, int pass, int use_pattern, co
 // blocks per SM (a larger bucket whose shared memory would cost the smaller
 // ones occupancy gets a launch of its own).  Returns the number of groups; group g is
 // [lo[g], hi[g]].
-static int bt_groups(int top, const BtWidths& wd, int* lo, int* hi) {
+static int bt_groups(int top, const BtWidths& wd, int sh, int* lo, int* hi) {
     int ng = 0;
     for (int b = 0; b <= top; ++b) {
         if (ng > 0) {
             const int g = ng - 1;
-            const int occ_g = bt_group_occupancy(lo[g], hi[g], wd, nullptr);
-            const int occ_b = bt_group_occupancy(b, b, wd, nullptr);
-            const int occ_m = bt_group_occupancy(lo[g], b, wd, nullptr);
+            const int occ_g = bt_group_occupancy(lo[g], hi[g], wd, sh, nullptr);
+            const int occ_b = bt_group_occupancy(b, b, wd, sh, nullptr);
+            const int occ_m = bt_group_occupancy(lo[g], b, wd, sh, nullptr);
             if (occ_m >= 1 && occ_m == occ_g && occ_m == occ_b) {
                 hi[g] = b;
                 continue;
@@ -962,7 +949,7 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
     for (int pass = 0; pass < (pattern ? 2 : 1); ++pass) {
         const BtWidths& wd = pass == 0 ? first : tuned;
         int glo[BT_NBUCKETS], ghi[BT_NBUCKETS];
-        const int ng = bt_groups(top, wd, glo, ghi);
+        const int ng = bt_groups(top, wd, bt_fold_params(f).nshift, glo, ghi);
         for (int g = ng - 1; g >= 0; --g) {   // largest systems first
             s = launch_group(glo[g], ghi[g], pass, pass == 0 && pattern ? 1 : 0, wd, d_data, d_offsets, d_m, d_n,
                              d_ld, d_nsearch, order, f, d_ranks, d_pivots, d_piv_offsets, d_status, bs, pat_J,
@@ -1087,6 +1074,18 @@ linac_status batched_tune(const Field& f, int32_t* nb_out, cudaStream_t stream) 
             if (ptr) cudaFree(ptr);
         if (st != LINAC_OK) return st;
     }
+    return LINAC_OK;
+}
+
+linac_status batched_set_nb(const int32_t* nb) {
+    int max_smem = 0;
+    LINAC_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
+    for (int b = 0; b < BT_NBUCKETS; ++b) {
+        const int v = nb[b];
+        if (v != 0 && v != 16 && v != 32 && v != 64) return LINAC_ERR_ARG;
+        if (v && bt_shared_bytes(b, v) + 4096 > (size_t)max_smem) return LINAC_ERR_UNSUPPORTED;
+    }
+    for (int b = 0; b < BT_NBUCKETS; ++b) bt_set_bucket_nb(b, nb[b]);
     return LINAC_OK;
 }
 

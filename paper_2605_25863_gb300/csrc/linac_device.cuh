@@ -107,6 +107,66 @@ __device__ __forceinline__ uint32_t reduce_signed(int64_t acc, const Field& f) {
     return reduce64((uint64_t)(t + (int64_t)off), f);
 }
 
+// Fold of a signed lazy accumulator with shifts and adds.  When c32 = 2^32
+// mod p has at most three set bits (2^e0 + 2^e1 + 2^e2; 2^31 - 1 gives 2,
+// 2^31 - 19 gives 38) H*c32 is formed on the ALU pipe, leaving the integer
+// multiply pipe to the products.  SHIFTS = 0 selects the multiply-pipe fold
+// (any p).  alu_reduce marks primes for which reduce_alu below is exact.
+struct FoldShifts {
+    uint32_t e[3];      // shift of each set bit of c32
+    uint32_t s[3];      // arithmetic right shift giving the high word of h * 2^e
+    int32_t alu_reduce; // reduce_alu is exact for this p
+    int32_t pad;
+};
+
+template <int SHIFTS>
+__device__ __forceinline__ int64_t fold_any(int64_t acc, const Field& f, const FoldShifts& fs) {
+    if (SHIFTS == 0) return fold64_fast(acc, f);
+    // acc = hi:lo; result = lo + sum_i sext(hi) * 2^e_i as a 64-bit carry chain
+    // of 32-bit shifts and adds, written out so it stays on the ALU pipe
+    uint32_t lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(acc));
+    uint32_t rlo = lo, rhi = 0;
+#pragma unroll
+    for (int i = 0; i < SHIFTS; ++i) {
+        asm("{\n\t.reg .u32 t, u;\n\t"
+            "shl.b32 t, %2, %3;\n\t"
+            "shr.s32 u, %2, %4;\n\t"
+            "add.cc.u32 %0, %0, t;\n\t"
+            "addc.u32 %1, %1, u;\n\t}"
+            : "+r"(rlo), "+r"(rhi)
+            : "r"(hi), "r"(fs.e[i]), "r"(fs.s[i]));
+    }
+    int64_t out;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(out) : "r"(rlo), "r"(rhi));
+    return out;
+}
+
+// Canonical residue of a signed 64-bit accumulator (|acc| < 2^63) without
+// multiplies, for SHIFTS > 0 and fs.alu_reduce.  Two folds bring acc to
+//   t2 = L2 + H2*c32 with H2 in [-(c32+1)/2, c32/2 + 1], so
+//   t2 in [-c32 (c32+1)/2, 2^32 - 1 + c32 (c32/2 + 1)];
+// the host sets alu_reduce only when c32 (c32+1)/2 <= p and
+// 2^32 - 1 + c32 (c32/2 + 1) < 3p, so u = t2 + p lies in [0, 4p) and two
+// conditional subtractions (2p, then p) finish.
+template <int SHIFTS>
+__device__ __forceinline__ uint32_t reduce_alu(int64_t acc, const Field& f, const FoldShifts& fs) {
+    const int64_t t2 = fold_any<SHIFTS>(fold_any<SHIFTS>(acc, f, fs), f, fs);
+    uint64_t u = (uint64_t)(t2 + (int64_t)f.p);
+    const uint64_t p2 = 2ull * f.p;
+    if (u >= p2) u -= p2;
+    if (u >= f.p) u -= f.p;
+    return (uint32_t)u;
+}
+
+// Canonical residue of a lazy accumulator: the multiply-free reduction when it
+// applies, the Barrett reduction otherwise.
+template <int SHIFTS>
+__device__ __forceinline__ uint32_t reduce_acc(int64_t acc, const Field& f, const FoldShifts& fs) {
+    if (SHIFTS > 0 && fs.alu_reduce) return reduce_alu<(SHIFTS > 0 ? SHIFTS : 1)>(acc, f, fs);
+    return reduce_signed(acc, f);
+}
+
 // Modular inverse of a (0 < a < p, p odd) by the binary extended Euclidean
 // algorithm (Stein's binary gcd, Knuth TAOCP vol. 2 sec. 4.5.2, carrying
 // Bezout coefficients): invariants x1*a = u and x2*a = v (mod p); halving a

@@ -13,6 +13,11 @@ namespace linac {
 // Constants for the prime p (see Field in linac_device.cuh).
 Field make_field(uint32_t p);
 
+// Shift parameters of fold_any / reduce_alu for p (linac_device.cuh).
+// Returns the number of set bits of 2^32 mod p when it is at most three
+// (0 = use the multiply-pipe fold, and reduce_alu does not apply).
+int fold_shifts(const Field& f, FoldShifts* fs);
+
 // Deterministic Miller-Rabin for 32-bit n with bases 2, 7, 61 (these three
 // bases have no common strong pseudoprime below 4,759,123,141; Jaeschke 1993).
 bool is_prime_u32(uint32_t n);
@@ -77,5 +82,6 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
 // 1024) time the feasible panel widths and keep the fastest for this device.
 linac_status batched_tune(const Field& f, int32_t* nb_out, cudaStream_t stream);
 void batched_get_nb(int32_t* nb_out);
+linac_status batched_set_nb(const int32_t* nb);
 
 }  // namespace linac

@@ -23,7 +23,8 @@ double g_ms[PROF_NCLASSES];
 long long g_count[PROF_NCLASSES];
 const char* g_names[PROF_NCLASSES] = {"init", "panel", "gather_f", "gather_w", "inverse", "trsm", "move",
                                       "update_plain", "update_limb", "limb_split", "finish", "batched",
-                                      "solve_pack", "solve_extract", "validate", "pattern"};
+                                      "solve_pack", "solve_extract", "validate", "pattern", "matmul",
+                                      "load_matrix", "derived"};
 
 cudaEvent_t take_event() {
     if (!g_pool.empty()) {

@@ -7,12 +7,10 @@
 // after every FOLD products the accumulator H*2^32 + L is folded to
 // H*(2^32 mod p) + L, which keeps |acc| < 2^62 + 2^32 so that FOLD more
 // products stay below 2^63 (the host derives FOLD >= 4 from p; FOLD = 8 for
-// the pseudo-Mersenne primes 2^31 - 1 and 2^31 - 19).  One Barrett reduction
-// per output and panel finishes the job.  No floating point anywhere.
-//
-// Tiling: 128 x 128 output tile per 256-thread block, 8 x 8 outputs per
-// thread (two 4-row and two 4-column groups so shared-memory reads are 128-bit
-// and conflict free), K in chunks of 16 staged by cp.async double buffering.
+// the pseudo-Mersenne primes 2^31 - 1 and 2^31 - 19).  One reduction per
+// output and panel finishes the job: two more folds and conditional
+// subtractions when 2^32 mod p is sparse (reduce_alu), Barrett otherwise.
+// No floating point anywhere.
 #include <algorithm>
 
 #include "linac_host.h"
@@ -20,39 +18,6 @@
 #include "update.cuh"
 
 namespace linac {
-
-// Fold of a signed lazy accumulator.  SHIFTS = 0: H*c32 + L on the integer
-// multiply pipe (any p).  SHIFTS = 1..3: c32 = 2^32 mod p has SHIFTS set bits
-// (2^e0 + 2^e1 + 2^e2), and H*c32 is formed with shifts and adds on the ALU
-// pipe, leaving the multiply pipe to the products (2^31 - 1 gives c32 = 2,
-// 2^31 - 19 gives c32 = 38).
-struct FoldShifts {
-    uint32_t e[3];   // shift of each set bit of c32
-    uint32_t s[3];   // arithmetic right shift giving the high word of h * 2^e
-};
-
-template <int SHIFTS>
-__device__ __forceinline__ int64_t fold_any(int64_t acc, const Field& f, const FoldShifts& fs) {
-    if (SHIFTS == 0) return fold64_fast(acc, f);
-    // acc = hi:lo; result = lo + sum_i sext(hi) * 2^e_i as a 64-bit carry chain
-    // of 32-bit shifts and adds, written out so it stays on the ALU pipe
-    uint32_t lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(acc));
-    uint32_t rlo = lo, rhi = 0;
-#pragma unroll
-    for (int i = 0; i < SHIFTS; ++i) {
-        asm("{\n\t.reg .u32 t, u;\n\t"
-            "shl.b32 t, %2, %3;\n\t"
-            "shr.s32 u, %2, %4;\n\t"
-            "add.cc.u32 %0, %0, t;\n\t"
-            "addc.u32 %1, %1, u;\n\t}"
-            : "+r"(rlo), "+r"(rhi)
-            : "r"(hi), "r"(fs.e[i]), "r"(fs.s[i]));
-    }
-    int64_t out;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(out) : "r"(rlo), "r"(rhi));
-    return out;
-}
 
 // MODE 0: trailing update of M (rows [r, r+k) receive R).  MODE 1: plain
 // product written as balanced residues to Out (k_pad x ldOut); M, m, c0 unused
@@ -147,7 +112,7 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
             const int64_t col = col0 + tx * 4;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (col + q < ncols) Out[row * ldOut + col + q] = to_balanced(reduce_signed(acc[i][q], f), f);
+                if (col + q < ncols) Out[row * ldOut + col + q] = to_balanced(reduce_acc<SHIFTS>(acc[i][q], f, fs), f);
         }
         return;
     }
@@ -168,11 +133,11 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
             const uint4 cv = *reinterpret_cast<const uint4*>(dst);
             const uint32_t c4[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) out[q] = submod(c4[q], reduce_signed(acc[i][q], f), f);
+            for (int q = 0; q < 4; ++q) out[q] = submod(c4[q], reduce_acc<SHIFTS>(acc[i][q], f, fs), f);
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                out[q] = col + q < ncols ? submod(dst[q], reduce_signed(acc[i][q], f), f) : 0u;
+                out[q] = col + q < ncols ? submod(dst[q], reduce_acc<SHIFTS>(acc[i][q], f, fs), f) : 0u;
         }
         if (col + 4 <= ncols) {
             *reinterpret_cast<uint4*>(dst) = make_uint4(out[0], out[1], out[2], out[3]);
@@ -183,20 +148,6 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
 }
 
 namespace {
-// Set bits of c32 when there are at most three of them (0 = use the multiply fold).
-int fold_shifts(const Field& f, FoldShifts* fs) {
-    uint32_t c = f.c32;
-    int n = 0;
-    for (int b = 0; b < 32; ++b)
-        if ((c >> b) & 1u) {
-            if (n == 3) return 0;
-            fs->e[n++] = (uint32_t)b;
-        }
-    for (int i = n; i < 3; ++i) fs->e[i] = 0;
-    for (int i = 0; i < 3; ++i) fs->s[i] = fs->e[i] == 0 ? 31u : 32u - fs->e[i];
-    return n;
-}
-
 template <int MODE>
 void launch_plain(dim3 grid, cudaStream_t stream, uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0,
                   const Field& f, const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,

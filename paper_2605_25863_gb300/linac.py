@@ -89,10 +89,17 @@ def lib():
         L.linac_batched_tune.restype = ctypes.c_int
         L.linac_batched_panel_widths.argtypes = [ctypes.c_void_p]
         L.linac_batched_panel_widths.restype = ctypes.c_int
+        L.linac_batched_set_panel_widths.argtypes = [ctypes.c_void_p]
+        L.linac_batched_set_panel_widths.restype = ctypes.c_int
         L.linac_launch_count.argtypes = []
         L.linac_launch_count.restype = ctypes.c_longlong
+        L.linac_load_matrix.argtypes = [vp, i64, i64, i64, vp, i64, i32, u32, vp, i64, vp]
+        L.linac_matmul.argtypes = [vp, i64, i64, i64, vp, i64, i64, u32, vp, i64, vp]
+        L.linac_null_space.argtypes = [vp, i64, i64, i64, vp, vp, u32, vp, i64, i64, vp, vp, vp]
+        L.linac_rank_factor.argtypes = [vp, i64, i64, i64, vp, vp, vp, i64, i64, vp]
         for name in ("linac_rref", "linac_rref_ex", "linac_solve", "linac_solve_ex",
-                     "linac_rref_batched", "linac_last_device_status", "linac_version"):
+                     "linac_rref_batched", "linac_last_device_status", "linac_version",
+                     "linac_load_matrix", "linac_matmul", "linac_null_space", "linac_rank_factor"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -230,6 +237,71 @@ def linac_rref_batched(data: torch.Tensor, offsets: torch.Tensor, m: torch.Tenso
     return ranks[:batch], pivots, piv_off, status[:batch]
 
 
+def linac_load_matrix(bases: torch.Tensor, lindices: torch.Tensor, p: int, *, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """A[r][c] = prod_t bases[r][lindices[c][t]] mod p (paper sections 2.3 and
+    3.3): rows are sampling points, columns monomials.  lindices is an
+    n_cols x d int32 CUDA tensor (contiguous)."""
+    pb, n_rows, n_basis, ldb = _matrix(bases, "bases")
+    if lindices.dim() != 2 or lindices.dtype != torch.int32 or not lindices.is_contiguous() or not lindices.is_cuda:
+        raise ValueError("lindices must be a contiguous n_cols x d int32 CUDA tensor")
+    n_cols, d = lindices.shape
+    if out is None:
+        out = padded(n_rows, n_cols, bases.device)
+    po, ro, co, ldo = _matrix(out, "out")
+    if (ro, co) != (n_rows, n_cols):
+        raise ValueError("out has the wrong shape")
+    _check(lib().linac_load_matrix(pb, n_rows, n_basis, ldb, lindices.data_ptr(), n_cols, d, p, po, ldo,
+                                   _stream_ptr(stream)), "linac_load_matrix")
+    return out
+
+
+def linac_matmul(A: torch.Tensor, B: torch.Tensor, p: int, *, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """A B mod p for canonical residues (exact)."""
+    pa, m, K, lda = _matrix(A, "A")
+    pb, kb, n, ldb = _matrix(B, "B")
+    if kb != K:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        out = padded(m, n, A.device)
+    pc, mc, nc, ldc = _matrix(out, "out")
+    if (mc, nc) != (m, n):
+        raise ValueError("out has the wrong shape")
+    _check(lib().linac_matmul(pa, m, K, lda, pb, n, ldb, p, pc, ldc, _stream_ptr(stream)), "linac_matmul")
+    return out
+
+
+def linac_null_space(R: torch.Tensor, rank: torch.Tensor, pivots: torch.Tensor, p: int, *,
+                     kcols: int | None = None, stream=None):
+    """Canonical null-space basis of an RREF (paper section 5.1).  Returns
+    (K, free, nullity): K is n x kcols (kcols defaults to n), valid in its
+    first nullity columns; free lists the free columns, -1 after them."""
+    pr, m, n, ld = _matrix(R, "R")
+    kc = n if kcols is None else int(kcols)
+    K = padded(n, max(kc, 1), R.device)[:, :kc] if n else padded(1, 1, R.device)[:0, :0]
+    free = torch.full((max(n, 1),), -1, dtype=torch.int32, device=R.device)
+    nullity = torch.zeros(1, dtype=torch.int32, device=R.device)
+    ldk = K.stride(0) if n else 1
+    _check(lib().linac_null_space(pr, m, n, ld, rank.data_ptr(), pivots.data_ptr(), p,
+                                  K.data_ptr() if n else None, kc, max(ldk, kc), free.data_ptr(), nullity.data_ptr(),
+                                  _stream_ptr(stream)), "linac_null_space")
+    return K, free[:n], nullity
+
+
+def linac_rank_factor(A: torch.Tensor, rank: torch.Tensor, pivots: torch.Tensor, *, ccols: int | None = None,
+                      stream=None) -> torch.Tensor:
+    """C = A[:, J] for the pivot columns J of A's RREF (paper section 5.1:
+    A = C R).  A is the original matrix.  Returns m x ccols (default
+    min(m, n)); columns at or beyond the rank are zero."""
+    pa, m, n, ld = _matrix(A, "A")
+    cc = min(m, n) if ccols is None else int(ccols)
+    C = padded(m, max(cc, 1), A.device)[:, :cc]
+    _check(lib().linac_rank_factor(pa, m, n, ld, rank.data_ptr(), pivots.data_ptr(), C.data_ptr(), cc,
+                                   max(C.stride(0), cc), _stream_ptr(stream)), "linac_rank_factor")
+    return C
+
+
 def linac_last_device_status(stream=None) -> int:
     return int(lib().linac_last_device_status(_stream_ptr(stream)))
 
@@ -274,6 +346,12 @@ def linac_batched_tune(p: int, stream=None) -> list[int]:
     out = (ctypes.c_int32 * 5)()
     _check(lib().linac_batched_tune(p, out, _stream_ptr(stream)), "linac_batched_tune")
     return list(out)
+
+
+def linac_batched_set_panel_widths(widths) -> None:
+    """Panel width per size bucket (5 entries: 16, 32, 64 or 0 = default)."""
+    arr = (ctypes.c_int32 * 5)(*[int(w) for w in widths])
+    _check(lib().linac_batched_set_panel_widths(arr), "linac_batched_set_panel_widths")
 
 
 def linac_batched_panel_widths() -> list[int]:

@@ -69,3 +69,26 @@ def test_batched_rejects_oversize(lib):
                                   2**31 - 1, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x1000),
                                   ctypes.c_void_p(0x1000), None, None)
     assert code == 8   # LINAC_ERR_UNSUPPORTED
+
+
+def test_construction_and_derived_entry_points_check_arguments(lib):
+    """linac_load_matrix, linac_matmul, linac_null_space, linac_rank_factor:
+    host-side rejections happen before any CUDA call."""
+    fake = ctypes.c_void_p(0x1000)
+    P = 2**31 - 1
+    # load_matrix: negative sizes, ld too small, d < 0, bad prime
+    assert lib.linac_load_matrix(fake, -1, 3, 3, fake, 4, 2, P, fake, 4, None) == 1
+    assert lib.linac_load_matrix(fake, 2, 3, 2, fake, 4, 2, P, fake, 4, None) == 1
+    assert lib.linac_load_matrix(fake, 2, 3, 3, fake, 4, -1, P, fake, 4, None) == 1
+    assert lib.linac_load_matrix(fake, 2, 3, 3, fake, 4, 2, 15, fake, 4, None) == 2
+    # matmul: inner/leading dimensions, null output, bad prime
+    assert lib.linac_matmul(fake, 2, 3, 2, fake, 4, 4, P, fake, 4, None) == 1
+    assert lib.linac_matmul(fake, 2, 3, 3, fake, 4, 4, P, None, 4, None) == 1
+    assert lib.linac_matmul(fake, 2, 3, 3, fake, 4, 4, 2**31, fake, 4, None) == 2
+    # null space: ldK < kcols, missing outputs, bad prime
+    assert lib.linac_null_space(fake, 3, 4, 4, fake, fake, P, fake, 4, 2, fake, fake, None) == 1
+    assert lib.linac_null_space(fake, 3, 4, 4, fake, fake, P, fake, 4, 4, None, fake, None) == 1
+    assert lib.linac_null_space(fake, 3, 4, 4, fake, fake, 9, fake, 4, 4, fake, fake, None) == 2
+    # rank factor: ld < n, ldC < ccols
+    assert lib.linac_rank_factor(fake, 3, 4, 3, fake, fake, fake, 3, 4, None) == 1
+    assert lib.linac_rank_factor(fake, 3, 4, 4, fake, fake, fake, 3, 2, None) == 1
