@@ -67,6 +67,13 @@ Field make_field(uint32_t p) {
     const unsigned __int128 room = (((unsigned __int128)1) << 63) - 1 - amax;
     unsigned __int128 k = prod ? room / prod : 1024;
     f.fold = (uint32_t)std::min<unsigned __int128>(k, 1024);
+    // Montgomery constants: p^(-1) mod 2^32 by Newton's iteration (each step
+    // doubles the number of correct low bits; p is odd, so p is its own
+    // inverse mod 8), then R^2 mod p = (2^32 mod p)^2 mod p
+    uint32_t inv = p;
+    for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
+    f.pinv = 0u - inv;
+    f.r2 = (uint32_t)(((uint64_t)f.c32 * f.c32) % p);
     return f;
 }
 

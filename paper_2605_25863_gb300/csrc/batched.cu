@@ -123,7 +123,7 @@ __host__ __device__ inline BtLayout bt_layout(int mmax, int nb) {
 
 template <int NB>
 struct BtSmall {
-    int J[NB], Pi[NB], own[NB], srcs[NB], dsts[NB];
+    int J[NB], Pi[NB], own[NB], srcs[NB], dsts[NB], colt[NB];
     uint32_t hinv[NB], hs[NB];
     int red[BT_THREADS / 32];
     int red2[2][BT_THREADS / 32];
@@ -188,6 +188,11 @@ struct BtFold {
 // hd_i of an earlier pivot row.  At the end pivot row t is zero at every other
 // pivot column and hd_t at its own, so E[t][u] = a_{t u} / hd_t gives E G = I.
 //
+// The slab holds every value in Montgomery form (x R mod p, R = 2^32), so each
+// update h * row_i - f * row_q is two 32 x 32 products and one Montgomery
+// reduction; zero tests are unaffected, and E[t][u] = a_{t u} / hd_t is the
+// same from the held values because the factors R cancel.
+//
 // The w - cc - 1 panel columns and s + 1 <= cc + 1 coefficients that change
 // at column cc fit in NB slab columns, so the block is laid out as NB
 // columns by BT_THREADS / NB row groups, and column slot cp of a thread names
@@ -216,9 +221,9 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
         const int i = e / (2 * NB), c = e % (2 * NB);
         const int64_t arow = forced ? (int64_t)sm.Pi[i] : (int64_t)(r + i);
         const uint32_t v = c < w ? A[arow * ld + c0 + c] : 0u;
-        G[i * SWG + c] = v;
+        G[i * SWG + c] = to_mont(v, f);
         if (c == 0) {
-            sig[i] = 1u;
+            sig[i] = f.c32;   // R mod p: the held form of 1
             hd[i] = 0u;
             isp[i] = 0;
             if (v != 0u && i < cand) cand = i;
@@ -273,12 +278,12 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
                 for (int u = 0; u < U; ++u) {
                     const int i = i0 + u * RGN;
                     if (act && fi[u] != 0u) {
-                        x[u] = mul2add(h, x[u], f.p - fi[u], pv, f);
+                        x[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
                         G[i * SWG + col] = x[u];
                         if (col_s) {
                             const bool prow = forced ? i < s : isp[i] != 0;
-                            if (prow) hd[i] = mulmod(h, hd[i], f);
-                            else sig[i] = mulmod(h, sig[i], f);
+                            if (prow) hd[i] = mont_mul(h, hd[i], f);
+                            else sig[i] = mont_mul(h, sig[i], f);
                         }
                     }
                     if (cand_col && x[u] != 0u && i < rows && i != qq && !isp[i] && i < cand) cand = i;
@@ -427,12 +432,34 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             if (bt_window_gj<NB>(A, ld, r, c0, w, k, 1, 1, f, P, isp, sm, Et) < 0) return false;
         }
         if (k == 0) continue;
-        // multipliers F (original entries at the pivot columns); loads unrolled
-        // so several are in flight per thread
-#pragma unroll 4
-        for (int e = tid; e < k * m; e += BT_THREADS) {
-            const int t = e / m, i = e - t * m;
-            Ft[t * ldF + i] = to_balanced(A[(int64_t)i * ld + sm.J[t]], f);
+        // multipliers F (original entries at the pivot columns, all of which lie
+        // in the panel's w columns): each row's panel segment is read as
+        // 16-byte words, coalesced, and every entry of a pivot column is
+        // written to F through the column -> pivot map colt
+        for (int j = tid; j < NB; j += BT_THREADS) sm.colt[j] = -1;
+        __syncthreads();
+        for (int t = tid; t < k; t += BT_THREADS) sm.colt[sm.J[t] - c0] = t;
+        __syncthreads();
+        {
+            const int wq = (w + 3) >> 2;
+#pragma unroll 2
+            for (int e = tid; e < m * wq; e += BT_THREADS) {
+                const int i = e / wq, q = e - i * wq;
+                const uint32_t* src = A + (int64_t)i * ld + c0 + 4 * q;
+                uint32_t v4[4];
+                if (vec_ok && 4 * q + 4 <= w) {
+                    const uint4 u = *reinterpret_cast<const uint4*>(src);
+                    v4[0] = u.x; v4[1] = u.y; v4[2] = u.z; v4[3] = u.w;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v4[u] = 4 * q + u < w ? src[u] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int t = 4 * q + u < w ? sm.colt[4 * q + u] : -1;
+                    if (t >= 0) Ft[t * ldF + i] = to_balanced(v4[u], f);
+                }
+            }
         }
         if (!e_ready) {
             for (int t = tid; t < k; t += BT_THREADS) {

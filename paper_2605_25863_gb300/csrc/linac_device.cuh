@@ -19,12 +19,15 @@ namespace linac {
 //                                    ("balanced" signed form, |x| <= half).
 //  fold = number of balanced products |x*y| <= half^2 that may be added to a
 //         folded accumulator without leaving the signed 64-bit range.
+//  pinv = -p^(-1) mod 2^32,  r2 = 2^64 mod p   Montgomery constants (R = 2^32).
 struct Field {
     uint32_t p;
     uint32_t c32;
     uint64_t mu;
     uint32_t half;
     uint32_t fold;
+    uint32_t pinv;
+    uint32_t r2;
 };
 
 __host__ __device__ inline uint32_t lo32(uint64_t x) { return (uint32_t)x; }
@@ -166,6 +169,32 @@ __device__ __forceinline__ uint32_t reduce_acc(int64_t acc, const Field& f, cons
     if (SHIFTS > 0 && fs.alu_reduce) return reduce_alu<(SHIFTS > 0 ? SHIFTS : 1)>(acc, f, fs);
     return reduce_signed(acc, f);
 }
+
+// Montgomery arithmetic with R = 2^32 (P. L. Montgomery, "Modular
+// multiplication without trial division", Math. Comp. 44, 1985).  x is held as
+// x R mod p; zero stays zero, negation commutes with the map, and the product
+// of two held values reduced by mont_redc is the held value of the product.
+// mont_redc(t) = t R^(-1) mod p for t < p R: m = (t mod R) (-p^(-1)) mod R
+// makes t + m p divisible by R, and (t + m p) / R < 2p (p < 2^31 keeps
+// t + m p below 2^64), so one conditional subtraction finishes.
+__device__ __forceinline__ uint32_t mont_redc(uint64_t t, const Field& f) {
+    const uint32_t m = (uint32_t)t * f.pinv;
+    const uint64_t u = t + (uint64_t)m * f.p;
+    const uint32_t r = (uint32_t)(u >> 32);
+    return r >= f.p ? r - f.p : r;
+}
+
+// (a x + b y) R^(-1) mod p for a, x, b, y in [0, p): 2 p^2 < p R.
+__device__ __forceinline__ uint32_t mont_mul2add(uint32_t a, uint32_t x, uint32_t b, uint32_t y, const Field& f) {
+    return mont_redc((uint64_t)a * x + (uint64_t)b * y, f);
+}
+
+__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, const Field& f) {
+    return mont_redc((uint64_t)a * b, f);
+}
+
+// x -> x R mod p (x in [0, p)): x R^2 R^(-1).
+__device__ __forceinline__ uint32_t to_mont(uint32_t x, const Field& f) { return mont_mul(x, f.r2, f); }
 
 // Modular inverse of a (0 < a < p, p odd) by the binary extended Euclidean
 // algorithm (Stein's binary gcd, Knuth TAOCP vol. 2 sec. 4.5.2, carrying
