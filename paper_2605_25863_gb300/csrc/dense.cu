@@ -122,9 +122,13 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
     int nrows = 0;
     if (S > 0 && lo < m) nrows = (int)min((int64_t)S, m - lo);
 
+    // the slab, the published candidate rows and prow hold Montgomery forms
+    // x R mod p (R = 2^32): each fraction-free update is two products and one
+    // Montgomery reduction, and the pivot rows go back to plain residues when
+    // they are written to panelU
     for (int64_t e = tid; e < (int64_t)nrows * w; e += blockDim.x) {
         const int i = (int)(e / w), j = (int)(e % w);
-        P[i * SW + j] = M[(lo + i) * ld + c0 + j];
+        P[i * SW + j] = to_mont(M[(lo + i) * ld + c0 + j], f);
     }
     for (int i = tid; i < nrows; i += blockDim.x) isp[i] = 0;
     for (int t = tid; t < NB_MAX; t += blockDim.x) own[t] = -1;
@@ -210,7 +214,7 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
             uint32_t* row = P + i * SW;
             if (q != INT_MAX) {
                 const uint32_t fi = row[cc];
-                if (fi != 0) row[cc + 1] = mul2add(h, row[cc + 1], f.p - fi, prow[cc + 1], f);
+                if (fi != 0) row[cc + 1] = mont_mul2add(h, row[cc + 1], f.p - fi, prow[cc + 1], f);
             }
             if (row[cc + 1] != 0 && i < ci) ci = i;
         }
@@ -221,7 +225,7 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
                 uint32_t* row = P + imin * SW;
                 const uint32_t fi = row[cc];
                 if (fi != 0)
-                    for (int j = cc + 2 + lane; j < w; j += 32) row[j] = mul2add(h, row[j], f.p - fi, prow[j], f);
+                    for (int j = cc + 2 + lane; j < w; j += 32) row[j] = mont_mul2add(h, row[j], f.p - fi, prow[j], f);
                 __syncwarp();
             }
             publish_and_wait(cc + 1, imin);
@@ -233,7 +237,7 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
                 const uint32_t fi = row[cc];
                 if (fi == 0) continue;
                 const uint32_t nf = f.p - fi;
-                for (int j = cc + 2 + lane; j < w; j += 32) row[j] = mul2add(h, row[j], nf, prow[j], f);
+                for (int j = cc + 2 + lane; j < w; j += 32) row[j] = mont_mul2add(h, row[j], nf, prow[j], f);
             }
         }
         __syncthreads();
@@ -243,7 +247,7 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
     for (int t = 0; t < kk; ++t) {
         const int i = own[t];
         if (i < 0) continue;
-        for (int j = tid; j < w; j += blockDim.x) panelU[(size_t)t * NB_MAX + j] = P[i * SW + j];
+        for (int j = tid; j < w; j += blockDim.x) panelU[(size_t)t * NB_MAX + j] = mont_redc(P[i * SW + j], f);
     }
     if (b == 0 && tid == 0) st->k = kk;
 }
@@ -347,16 +351,20 @@ einv_kernel(const DenseState* __restrict__ st, const uint32_t* __restrict__ pane
         hinv[t] = st->hinv[t];
     }
     __syncthreads();
-    for (int t = tid; t < k; t += blockDim.x) hs[t] = panelU[(size_t)t * NB_MAX + Jl[t]];
+    // the recurrence runs on Montgomery forms x R mod p (R = 2^32): each step
+    // is two products and one Montgomery reduction; E leaves in plain form
+    for (int t = tid; t < k; t += blockDim.x) hs[t] = to_mont(panelU[(size_t)t * NB_MAX + Jl[t]], f);
     for (int e = tid; e < k * k; e += blockDim.x) {
         const int t = e / k, s = e % k;
         const uint32_t v = panelU[(size_t)t * NB_MAX + Jl[s]];
-        Co[t * S + s] = s > t ? mulmod(v, hinv[t], f) : v;
+        Co[t * S + s] = to_mont(s > t ? mulmod(v, hinv[t], f) : v, f);
     }
     for (int e = tid; e < k * C; e += blockDim.x) {
         const int t = e / C, c = e % C;
-        Ec[t * C + c] = (t == j0 + c) ? 1u : 0u;
+        Ec[t * C + c] = (t == j0 + c) ? f.c32 : 0u;   // the held form of 1 is R mod p
     }
+    __syncthreads();
+    for (int t = tid; t < k; t += blockDim.x) hinv[t] = to_mont(hinv[t], f);
     __syncthreads();
     // forward (all stages: row j itself is rescaled by h_s at every earlier
     // stage s whose multiplier f_js is nonzero, so E[j][j] changes before s = j)
@@ -365,17 +373,17 @@ einv_kernel(const DenseState* __restrict__ st, const uint32_t* __restrict__ pane
         for (int e = tid; e < (k - 1 - s) * C; e += blockDim.x) {
             const int t = s + 1 + e / C, c = e % C;
             const uint32_t fts = Co[t * S + s];
-            if (fts) Ec[t * C + c] = mul2add(h, Ec[t * C + c], f.p - fts, Ec[s * C + c], f);
+            if (fts) Ec[t * C + c] = mont_mul2add(h, Ec[t * C + c], f.p - fts, Ec[s * C + c], f);
         }
         __syncthreads();
     }
-    for (int e = tid; e < k * C; e += blockDim.x) Ec[e] = mulmod(Ec[e], hinv[e / C], f);
+    for (int e = tid; e < k * C; e += blockDim.x) Ec[e] = mont_mul(Ec[e], hinv[e / C], f);
     __syncthreads();
     for (int s = k - 1; s >= 1; --s) {
         for (int e = tid; e < s * C; e += blockDim.x) {
             const int t = e / C, c = e % C;
             const uint32_t cts = Co[t * S + s];
-            if (cts) Ec[t * C + c] = mul2add(1u, Ec[t * C + c], f.p - cts, Ec[s * C + c], f);
+            if (cts) Ec[t * C + c] = submod(Ec[t * C + c], mont_mul(cts, Ec[s * C + c], f), f);
         }
         __syncthreads();
     }
@@ -383,7 +391,7 @@ einv_kernel(const DenseState* __restrict__ st, const uint32_t* __restrict__ pane
     for (int e = tid; e < C * NB_MAX; e += blockDim.x) {
         const int c = e / NB_MAX, t = e % NB_MAX;
         const int j = j0 + c;
-        Et[(size_t)j * NB_MAX + t] = (j < k && t < k) ? to_balanced(Ec[t * C + c], f) : 0;
+        Et[(size_t)j * NB_MAX + t] = (j < k && t < k) ? to_balanced(mont_redc(Ec[t * C + c], f), f) : 0;
     }
 }
 
