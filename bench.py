@@ -103,6 +103,21 @@ def update_work(m: int, n: int, pivots, nb: int) -> int:
     return total
 
 
+def replica_rate(local_ms: float, local_work: float, world: int, device) -> tuple[float, float]:
+    """Whole-job rate of N independent replicas (weak scaling): every rank did
+    the same work; the job took as long as the slowest rank, so the time is
+    the maximum over ranks (an all-reduce on the process group when world > 1)
+    and the rate is world x work / that time.  Returns (rate, max_ms)."""
+    max_ms = local_ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    return world * local_work / (max_ms / 1000.0), max_ms
+
+
 def update_src_sha() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -318,12 +333,7 @@ def run_ours(args):
     piv = events[-1][3].cpu().numpy()[:rank_v]
     ok = rank_v == m and np.array_equal(piv, np.arange(m))
     work_macs = gj_work(m, n, piv)
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * work_macs * args.steps / (tot_ms / 1000.0)
+    value, tot_ms = replica_rate(sum(step_ms), work_macs * args.steps, world, dev)
 
     # dominant kernel: the trailing update
     upd_name = "update_limb" if args.path == "limb" else "update_plain"

@@ -9,6 +9,10 @@
 //                       its points' basis values in shared memory and every
 //                       thread owns monomials; here a block owns 8 points so
 //                       each monomial's indices are read once per 8 rows.
+//                       The product runs in Montgomery form: d Montgomery
+//                       multiplications give prod * R^(-d), and the running
+//                       value starts at R^d mod p instead of 1, so the result
+//                       is the plain product.
 //  matmul_mod_kernel    C = A B mod p with lazy signed 64-bit accumulation of
 //                       balanced residues (same arithmetic as the trailing
 //                       update); expands a template of polynomial entries at
@@ -38,8 +42,8 @@ constexpr int LM_SMEM_BASIS = 1536;         // basis values per point staged in 
 template <bool SMEM>
 __global__ void __launch_bounds__(LM_THREADS)
 load_matrix_kernel(const uint32_t* __restrict__ bases, int64_t n_rows, int n_basis, int64_t ldb,
-                   const int32_t* __restrict__ lind, int64_t n_cols, int d, Field f, uint32_t* __restrict__ A,
-                   int64_t lda, int* status) {
+                   const int32_t* __restrict__ lind, int64_t n_cols, int d, Field f, uint32_t rd,
+                   uint32_t* __restrict__ A, int64_t lda, int* status) {
     extern __shared__ uint32_t sb[];   // LM_ROWS x n_basis (SMEM only)
     const int64_t r0 = (int64_t)blockIdx.y * LM_ROWS;
     const int nr = (int)(n_rows - r0 < LM_ROWS ? n_rows - r0 : LM_ROWS);
@@ -54,7 +58,7 @@ load_matrix_kernel(const uint32_t* __restrict__ bases, int64_t n_rows, int n_bas
     if (c >= n_cols) return;
     uint32_t acc[LM_ROWS];
 #pragma unroll
-    for (int rr = 0; rr < LM_ROWS; ++rr) acc[rr] = 1u;
+    for (int rr = 0; rr < LM_ROWS; ++rr) acc[rr] = rd;   // R^d mod p
     bool bad = false;
     for (int t = 0; t < d; ++t) {
         const int idx = lind[c * d + t];
@@ -66,14 +70,14 @@ load_matrix_kernel(const uint32_t* __restrict__ bases, int64_t n_rows, int n_bas
         for (int rr = 0; rr < LM_ROWS; ++rr) {
             if (rr < nr) {
                 const uint32_t v = SMEM ? sb[rr * n_basis + idx] : bases[(r0 + rr) * ldb + idx];
-                acc[rr] = mulmod(acc[rr], v, f);
+                acc[rr] = mont_mul(acc[rr], v, f);
             }
         }
     }
     if (bad) atomicCAS(status, 0, (int)LINAC_ERR_RANGE);
 #pragma unroll
     for (int rr = 0; rr < LM_ROWS; ++rr)
-        if (rr < nr) A[(r0 + rr) * lda + c] = bad ? 0u : (d == 0 ? 1u % f.p : acc[rr]);
+        if (rr < nr) A[(r0 + rr) * lda + c] = bad ? 0u : acc[rr];
 }
 
 constexpr int MM_BM = 128, MM_BN = 64, MM_BK = 16;
@@ -297,6 +301,10 @@ linac_status linac_load_matrix(const uint32_t* d_bases, int64_t n_rows, int64_t 
     linac_status s = (linac_status)reset_status_word(stream, &status);
     if (s != LINAC_OK) return s;
     if (n_rows == 0 || n_cols == 0) return LINAC_OK;
+    // R^d mod p (R = 2^32 = c32 mod p): the start value that cancels the d
+    // factors R^(-1) of the Montgomery products
+    uint64_t rd = 1 % p;
+    for (int t = 0; t < d; ++t) rd = rd * f.c32 % p;
     const int64_t gy = (n_rows + LM_ROWS - 1) / LM_ROWS;
     if (gy > 65535) return LINAC_ERR_UNSUPPORTED;
     dim3 grid((unsigned)((n_cols + LM_THREADS - 1) / LM_THREADS), (unsigned)gy);
@@ -304,10 +312,10 @@ linac_status linac_load_matrix(const uint32_t* d_bases, int64_t n_rows, int64_t 
     if (n_basis <= LM_SMEM_BASIS) {
         const size_t smem = (size_t)LM_ROWS * n_basis * 4;
         load_matrix_kernel<true><<<grid, LM_THREADS, smem, stream>>>(d_bases, n_rows, (int)n_basis, ld_bases, d_lindices,
-                                                                     n_cols, d, f, d_A, ldA, status);
+                                                                     n_cols, d, f, (uint32_t)rd, d_A, ldA, status);
     } else {
         load_matrix_kernel<false><<<grid, LM_THREADS, 0, stream>>>(d_bases, n_rows, (int)n_basis, ld_bases, d_lindices,
-                                                                   n_cols, d, f, d_A, ldA, status);
+                                                                   n_cols, d, f, (uint32_t)rd, d_A, ldA, status);
     }
     LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;
