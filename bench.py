@@ -54,11 +54,11 @@ SM_MAX_MHZ = 2070.0       # GB300 maximum SM clock
 IMAD_WIDE_PER_SM_CLK = 32
 # DRAM bytes per output of update_plain_kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of the third panel of the
-# 8192 x 8448 elimination: 481.3 MB for 8192 x 8192 outputs; summary in
+# 8192 x 8448 elimination: 481.1 MB for 8192 x 8192 outputs; summary in
 # profiles/update_plain_rref_8192x8448.md), valid while the kernel's sources
 # hash to UPDATE_SRC_SHA; the traffic is reported as null otherwise
-UPDATE_BYTES_PER_OUTPUT = 481.3e6 / (8192 * 8192)
-UPDATE_SRC_SHA = "62e4e4d25e82826b"
+UPDATE_BYTES_PER_OUTPUT = 481.1e6 / (8192 * 8192)
+UPDATE_SRC_SHA = "480f9cad0db8f1ef"
 UPDATE_SRC = ["paper_2605_25863_gb300/csrc/update_plain.cu", "paper_2605_25863_gb300/csrc/linac_device.cuh",
               "paper_2605_25863_gb300/csrc/update.cuh"]
 
@@ -77,8 +77,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU oracle, path comparison and batched legs")
     ap.add_argument("--batch-count", type=int, default=10000)
-    ap.add_argument("--only", choices=["all", "batched"], default="all",
-                    help="batched: run the batched workload alone (a profiling aid; prints its own line)")
+    ap.add_argument("--only", choices=["all", "batched", "construction"], default="all",
+                    help="batched / construction: run that workload alone (a profiling aid; prints its own line)")
     ap.add_argument("--widths", default="",
                     help="comma-separated panel widths per size bucket for the batched legs (default: autotune)")
     ap.add_argument("--measure-peaks", action="store_true",
@@ -283,6 +283,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     if args.only == "batched":
         print(json.dumps({"batched": batched_leg(args, linac, synth, dev, stream)}), flush=True)
+        return 0
+    if args.only == "construction":
+        print(json.dumps({"construction": construction_leg(args, linac, synth, dev)}), flush=True)
         return 0
 
     m, rhs = args.m, args.rhs

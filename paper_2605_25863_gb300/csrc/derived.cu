@@ -44,13 +44,16 @@ __global__ void __launch_bounds__(LM_THREADS)
 load_matrix_kernel(const uint32_t* __restrict__ bases, int64_t n_rows, int n_basis, int64_t ldb,
                    const int32_t* __restrict__ lind, int64_t n_cols, int d, Field f, uint32_t rd,
                    uint32_t* __restrict__ A, int64_t lda, int* status) {
-    extern __shared__ uint32_t sb[];   // LM_ROWS x n_basis (SMEM only)
+    // SMEM: n_basis x LM_ROWS, basis-major, so the 8 points' values of one
+    // basis variable are two 16-byte words (rows beyond the last point are
+    // zero and never stored)
+    extern __shared__ __align__(16) uint32_t sb[];
     const int64_t r0 = (int64_t)blockIdx.y * LM_ROWS;
     const int nr = (int)(n_rows - r0 < LM_ROWS ? n_rows - r0 : LM_ROWS);
     if (SMEM) {
-        for (int e = threadIdx.x; e < nr * n_basis; e += LM_THREADS) {
+        for (int e = threadIdx.x; e < LM_ROWS * n_basis; e += LM_THREADS) {
             const int rr = e / n_basis, b = e - rr * n_basis;
-            sb[rr * n_basis + b] = bases[(r0 + rr) * ldb + b];
+            sb[b * LM_ROWS + rr] = rr < nr ? bases[(r0 + rr) * ldb + b] : 0u;
         }
         __syncthreads();
     }
@@ -66,12 +69,16 @@ load_matrix_kernel(const uint32_t* __restrict__ bases, int64_t n_rows, int n_bas
             bad = true;
             continue;
         }
+        if (SMEM) {
+            const uint4 lo = *reinterpret_cast<const uint4*>(sb + idx * LM_ROWS);
+            const uint4 hi = *reinterpret_cast<const uint4*>(sb + idx * LM_ROWS + 4);
+            const uint32_t v[LM_ROWS] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-        for (int rr = 0; rr < LM_ROWS; ++rr) {
-            if (rr < nr) {
-                const uint32_t v = SMEM ? sb[rr * n_basis + idx] : bases[(r0 + rr) * ldb + idx];
-                acc[rr] = mont_mul(acc[rr], v, f);
-            }
+            for (int rr = 0; rr < LM_ROWS; ++rr) acc[rr] = mont_mul(acc[rr], v[rr], f);
+        } else {
+#pragma unroll
+            for (int rr = 0; rr < LM_ROWS; ++rr)
+                if (rr < nr) acc[rr] = mont_mul(acc[rr], bases[(r0 + rr) * ldb + idx], f);
         }
     }
     if (bad) atomicCAS(status, 0, (int)LINAC_ERR_RANGE);
