@@ -27,6 +27,7 @@
 
 #include "linac_host.h"
 #include "profile.h"
+#include "update.cuh"
 
 namespace linac {
 
@@ -107,7 +108,7 @@ __host__ __device__ inline BtLayout bt_layout(int mmax, int nb) {
     L.ldF = (mmax + 7) / 8 * 8;
     const size_t panel = (size_t)mmax * (nb + 1) * 4;                 // panel slab (all rows)
     const size_t ftb = (size_t)nb * L.ldF * 4;                        // Ft[t][row], balanced
-    const size_t tiles = (size_t)3 * nb * BT_TB * 4;                  // V, X, R tiles
+    const size_t tiles = (size_t)4 * nb * BT_TB * 4;                  // V, X, R, next V tiles
     L.off_p = 0;
     L.off_ft = 0;
     L.off_tiles = ftb;
@@ -328,6 +329,7 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
     uint32_t* V = (uint32_t*)(smem + L.off_tiles);
     uint32_t* X = V + NB * BT_TB;
     int32_t* Rt = (int32_t*)(V + 2 * NB * BT_TB);
+    uint32_t* Vnext = V + 3 * NB * BT_TB;
     uint32_t* PU = (uint32_t*)(smem + L.off_pu);
     int32_t* Et = (int32_t*)(smem + L.off_e);
     uint32_t* E = (uint32_t*)Et;
@@ -533,18 +535,38 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             }
         }
         __syncthreads();
-        // column tiles
+        // column tiles.  The pivot rows' tile V (raw residues) is copied with
+        // cp.async one tile ahead, during the previous tile's update: the
+        // update writes only its own tile's columns, so the next tile of the
+        // pivot rows is already final.  Without 16-byte row alignment the
+        // copy is synchronous.
+        uint32_t* Vcur = V;
+        uint32_t* Vnxt = Vnext;
+        auto fetch_v = [&](int j0v, uint32_t* dst) {
+            const int twv = min(BT_TB, n - j0v);
+            if (vec_ok) {
+                for (int e = tid; e < kp * (BT_TB / 4); e += BT_THREADS) {
+                    const int t = e / (BT_TB / 4), j = (e % (BT_TB / 4)) * 4;
+                    const int bytes = (t < k && j < twv) ? min(4, twv - j) * 4 : 0;
+                    const uint32_t* src = bytes ? A + (int64_t)sm.Pi[t] * ld + j0v + j : A;
+                    cp_async16(dst + t * BT_TB + j, src, bytes);
+                }
+                cp_async_commit();
+            } else {
+                for (int e = tid; e < kp * BT_TB; e += BT_THREADS) {
+                    const int t = e / BT_TB, j = e % BT_TB;
+                    dst[t * BT_TB + j] = (t < k && j < twv) ? A[(int64_t)sm.Pi[t] * ld + j0v + j] : 0u;
+                }
+            }
+        };
+        fetch_v(c0, Vcur);
         for (int j0 = c0; j0 < n; j0 += BT_TB) {
             const int tw = min(BT_TB, n - j0);
-#pragma unroll 4
-            for (int e = tid; e < kp * BT_TB; e += BT_THREADS) {
-                const int t = e / BT_TB, j = e % BT_TB;
-                V[t * BT_TB + j] = (t < k && j < tw) ? (uint32_t)to_balanced(A[(int64_t)sm.Pi[t] * ld + j0 + j], f) : 0u;
-            }
             for (int e = tid; e < npairs * tw; e += BT_THREADS) {
                 const int a = e / tw, j = e % tw;
                 X[a * BT_TB + j] = A[(int64_t)sm.srcs[a] * ld + j0 + j];
             }
+            cp_async_wait<0>();
             __syncthreads();
             // R = E V, 4 x 4 outputs per thread (balanced operands, lazy signed accumulation)
             for (int e = tid; e < (kp / 4) * (BT_TB / 4); e += BT_THREADS) {
@@ -556,9 +578,10 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
                     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
                 for (int s2 = 0; s2 < kp; ++s2) {
                     const int4 ev = *reinterpret_cast<const int4*>(Et + s2 * NB + t0);
-                    const int4 vv = *reinterpret_cast<const int4*>(V + s2 * BT_TB + jq);
+                    const uint4 vv = *reinterpret_cast<const uint4*>(Vcur + s2 * BT_TB + jq);
                     const int ea[4] = {ev.x, ev.y, ev.z, ev.w};
-                    const int vb[4] = {vv.x, vv.y, vv.z, vv.w};
+                    const int vb[4] = {to_balanced(vv.x, f), to_balanced(vv.y, f), to_balanced(vv.z, f),
+                                       to_balanced(vv.w, f)};
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -580,6 +603,13 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
                 A[(int64_t)sm.dsts[a] * ld + j0 + j] = X[a * BT_TB + j];
             }
             __syncthreads();
+            // the next tile's V, in flight during this tile's update
+            if (j0 + BT_TB < n) fetch_v(j0 + BT_TB, Vnxt);
+            {
+                uint32_t* tmp = Vcur;
+                Vcur = Vnxt;
+                Vnxt = tmp;
+            }
             // update: rows in [r, r+k) receive R, every other row A -= F R
             // (MR rows x 4 columns per work item; MR = 8 for 64-column panels,
             // whose blocks own an SM alone, 4 otherwise so two blocks fit)
