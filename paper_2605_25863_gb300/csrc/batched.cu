@@ -134,13 +134,13 @@ struct BtSmall {
 // Block-wide minimum of one int per thread (INT_MAX = none).
 template <int NB>
 __device__ __forceinline__ int block_min(int v, BtSmall<NB>& sm) {
-    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    v = __reduce_min_sync(0xffffffffu, v);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) sm.red[warp] = v;
     __syncthreads();
     if (warp == 0) {
         int x = lane < BT_THREADS / 32 ? sm.red[lane] : INT_MAX;
-        for (int o = 16; o; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+        x = __reduce_min_sync(0xffffffffu, x);
         if (lane == 0) sm.s_min = x;
     }
     __syncthreads();
@@ -153,7 +153,7 @@ __device__ __forceinline__ int block_min(int v, BtSmall<NB>& sm) {
 // read it.
 template <int NB>
 __device__ __forceinline__ int block_min1(int v, BtSmall<NB>& sm, int& buf) {
-    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    v = __reduce_min_sync(0xffffffffu, v);
     if ((threadIdx.x & 31) == 0) sm.red2[buf][threadIdx.x >> 5] = v;
     __syncthreads();
     int x = INT_MAX;
@@ -211,7 +211,7 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
     constexpr int CW = NB;                  // column slots
     constexpr int RGN = BT_THREADS / CW;    // row groups
     constexpr int UMAX = (bt_win_rows(NB) + RGN - 1) / RGN;
-    constexpr int U = UMAX < 4 ? UMAX : 4;  // rows per batch of independent updates
+    constexpr int U = UMAX < 6 ? UMAX : 6;  // rows per batch of independent updates
     static_assert(BT_THREADS % CW == 0, "column slots must divide the block");
     const int tid = threadIdx.x;
     const int cp = tid % CW, rg = tid / CW;

@@ -80,13 +80,13 @@ __global__ void finish_kernel(DenseState* st, int32_t* d_pivots, int32_t* d_rank
 
 // Block-wide minimum of one int per thread.
 __device__ __forceinline__ int panel_block_min(int v, int* red, int* out) {
-    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    v = __reduce_min_sync(0xffffffffu, v);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = v;
     __syncthreads();
     if (warp == 0) {
         int x = lane < (int)(blockDim.x >> 5) ? red[lane] : INT_MAX;
-        for (int o = 16; o; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+        x = __reduce_min_sync(0xffffffffu, x);
         if (lane == 0) *out = x;
     }
     __syncthreads();
@@ -176,7 +176,7 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
         if (warp == 0) {
             int v = INT_MAX;
             for (int g = lane; g < G; g += 32) v = min(v, __ldcg(&cidx[par * G + g]));
-            for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+            v = __reduce_min_sync(0xffffffffu, v);
             if (lane == 0) s_q = v;
         }
         __syncthreads();
