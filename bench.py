@@ -401,20 +401,37 @@ def e2e_leg(args, linac, synth, pristine, work, m, n, p, nb, stream):
     host_in.copy_(pristine)
     host_out = torch.empty_like(host_in, pin_memory=True)
     steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
+    parts = []
+
+    def one_step(record):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
         work.copy_(host_in, non_blocking=True)
+        ev[1].record(stream)
         r, piv = linac.linac_rref(work, p, nb=nb, path=args.path)
+        ev[2].record(stream)
         host_out.copy_(work, non_blocking=True)
+        ev[3].record(stream)
         rk = r.to("cpu", non_blocking=True)
         pv = piv.to("cpu", non_blocking=True)
         torch.cuda.synchronize()
+        if record:
+            parts.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
+        return rk, pv
+
+    one_step(False)   # warm-up: the first transfers through freshly pinned buffers are slower
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rk, pv = one_step(True)
     dt = time.perf_counter() - t0
     macs = gj_work(m, n, pv.numpy()[:int(rk.item())])
     nbytes = host_in.numel() * 4
+    med = [statistics.median(x[i] for x in parts) for i in range(3)]
     return {"value": macs * steps / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-            "d2h_bytes_per_step": nbytes + 4 + 4 * m, "steps": steps, "ms_per_step": 1000 * dt / steps}
+            "d2h_bytes_per_step": nbytes + 4 + 4 * m, "steps": steps, "warmup": 1,
+            "ms_per_step": 1000 * dt / steps,
+            "parts_ms": {"h2d": med[0], "rref": med[1], "d2h": med[2]}}
 
 
 def path_leg(args, linac, pristine, work, m, n, p, nb, stream, main_value):

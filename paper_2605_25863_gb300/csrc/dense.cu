@@ -52,6 +52,7 @@ __global__ void init_kernel(DenseState* st, int32_t* d_pivots, int64_t npiv, int
         if (threadIdx.x == 0) {
             st->r = 0;
             st->k = 0;
+            st->win_ok = 0;
             st->bar.count = 0;
             st->bar.gen = 0;
             *d_rank = 0;
@@ -100,6 +101,104 @@ __device__ __forceinline__ int panel_block_min(int v, int* red, int* out) {
 // the panel, so the barrier latency overlaps the bulk of the elimination.
 // All arithmetic is the same fraction-free step as in the plain loop:
 // row_i <- h row_i - f_i pivot with f_i kept in column cc.
+// Pivots of a panel from a window of its first w + WIN_EXTRA remaining rows,
+// one block, no grid-wide synchronisation.  Every column's pivot is the
+// lowest-index remaining row with a nonzero entry (section 3.2: over a finite
+// field any nonzero entry serves, and the RREF does not depend on the choice),
+// and the window holds the lowest-index remaining rows: when it has a pivot in
+// every panel column, or holds every remaining row, its pivots, their order
+// and the pivot rows' fraction-free panel entries are exactly those the
+// grid-wide search in panel_kernel would find.  It then writes them (k, J,
+// Pi, panelU), advances panel_kernel's arrival counter by the w x G arrivals
+// that kernel would have made, and sets win_ok so that panel_kernel returns
+// at once; otherwise it leaves everything to panel_kernel.  Values are held in
+// Montgomery form, as in panel_kernel.
+__global__ void __launch_bounds__(WIN_THREADS)
+window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f, DenseState* st,
+              uint32_t* __restrict__ panelU, int G) {
+    extern __shared__ __align__(16) uint32_t P[];   // rows x (w + 1)
+    __shared__ int red[2][WIN_THREADS / 32];
+    __shared__ unsigned char isp[NB_MAX + WIN_EXTRA];
+    __shared__ int own[NB_MAX], Jl[NB_MAX];
+    constexpr int RG = WIN_THREADS / NB_MAX;        // row groups of the elimination
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int SW = w + 1;
+    const int64_t r = st->r;
+    const int64_t left = m - r > 0 ? m - r : 0;
+    const int rows = (int)(left < w + WIN_EXTRA ? left : w + WIN_EXTRA);
+    for (int e = tid; e < rows * w; e += WIN_THREADS) {
+        const int i = e / w, j = e - i * w;
+        P[i * SW + j] = to_mont(M[(r + i) * ld + c0 + j], f);
+    }
+    for (int i = tid; i < rows; i += WIN_THREADS) isp[i] = 0;
+    __syncthreads();
+    int kk = 0, buf = 0;
+    const int jj = tid % NB_MAX, rg = tid / NB_MAX;
+    for (int cc = 0; cc < w; ++cc) {
+        // the lowest remaining window row with a nonzero entry in column cc
+        int c = (tid < rows && !isp[tid] && P[tid * SW + cc] != 0u) ? tid : INT_MAX;
+        c = __reduce_min_sync(0xffffffffu, c);
+        if (lane == 0) red[buf][warp] = c;
+        __syncthreads();
+        int q = INT_MAX;
+#pragma unroll
+        for (int x = 0; x < WIN_THREADS / 32; ++x) q = min(q, red[buf][x]);
+        buf ^= 1;
+        if (q == INT_MAX) continue;   // no pivot in this column (the same for every thread)
+        const uint32_t h = P[q * SW + cc];
+        if (tid == 0) {
+            isp[q] = 1;
+            own[kk] = q;
+            Jl[kk] = cc;
+        }
+        ++kk;
+        // fraction-free elimination of column cc from the other remaining
+        // rows: row_i <- h row_i - f_i row_q on the columns right of cc
+        const int nc = w - cc - 1;
+        if (jj < nc) {
+            // six independent rows per batch: all loads, then the products,
+            // then the stores, so the batch's latencies overlap
+            constexpr int U = 6;
+            const int j = cc + 1 + jj;
+            const uint32_t pv = P[q * SW + j];
+            for (int i0 = rg; i0 < rows; i0 += U * RG) {
+                uint32_t fi[U], x[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * RG;
+                    const bool ok = i < rows && i != q && !isp[i];
+                    fi[u] = ok ? P[i * SW + cc] : 0u;
+                    x[u] = ok ? P[i * SW + j] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (fi[u] != 0u) x[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (fi[u] != 0u) P[(i0 + u * RG) * SW + j] = x[u];
+            }
+        }
+        __syncthreads();
+    }
+    if (kk == w || rows == left) {
+        for (int t = tid; t < kk; t += WIN_THREADS) {
+            st->J[t] = c0 + Jl[t];
+            st->Pi[t] = (int32_t)(r + own[t]);
+        }
+        for (int e = tid; e < kk * w; e += WIN_THREADS) {
+            const int t = e / w, j = e - t * w;
+            panelU[(size_t)t * NB_MAX + j] = mont_redc(P[own[t] * SW + j], f);
+        }
+        if (tid == 0) {
+            st->k = kk;
+            st->win_ok = 1;
+            atomicAdd(&st->bar.count, (unsigned)w * (unsigned)G);
+        }
+    } else if (tid == 0) {
+        st->win_ok = 0;
+    }
+}
+
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, int S_max,
              Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status) {
@@ -112,6 +211,7 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
     __shared__ int s_red[PANEL_THREADS / 32];
     __shared__ int s_min, s_q, s_ok;
 
+    if (st->win_ok) return;   // window_kernel found this panel's pivots (and advanced the barrier)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int G = gridDim.x, b = blockIdx.x;
     int* cidx = (int*)(cand + (size_t)2 * G * NB_MAX);   // [2][G] candidate row per block
@@ -573,6 +673,8 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
                                         (int)psmem));
     LINAC_CUDA_TRY(cudaFuncSetAttribute(einv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)EINV_SMEM));
+    LINAC_CUDA_TRY(cudaFuncSetAttribute(window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)WIN_SMEM));
     int occ = 0;
     LINAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_kernel, PANEL_THREADS, psmem));
     if (occ < 1 || G > occ * sm_count()) return LINAC_ERR_UNSUPPORTED;
@@ -601,6 +703,10 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
     for (int64_t c0 = 0; c0 < nsearch; c0 += nb) {
         const int w = (int)std::min<int64_t>(nb, nsearch - c0);
         const int64_t ncols = n - c0;
+        {
+            ProfScope ps(stream, PROF_PANEL);
+            window_kernel<<<1, WIN_THREADS, WIN_SMEM, stream>>>(dA, m, ld, (int)c0, w, f, st, panelU, G);
+        }
         {
             const uint32_t* Mc = dA;
             int64_t m_ = m, ld_ = ld;

@@ -18,7 +18,8 @@ constexpr int UPD_BK = 16;    // update K chunk; panel widths are multiples of i
 struct DenseState {
     int32_t r;              // rank so far = first row of the current panel's pivots
     int32_t k;              // pivots found in the current panel
-    int32_t pad0, pad1;
+    int32_t win_ok;         // the current panel's pivots came from window_kernel (panel_kernel skips)
+    int32_t pad1;
     GridBarrier bar;
     int32_t J[NB_MAX];      // pivot columns of the current panel (absolute)
     int32_t Pi[NB_MAX];     // pivot rows of the current panel (absolute, before the move)
