@@ -33,6 +33,8 @@
 #include <climits>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "dense_kernels.cuh"
 #include "linac_host.h"
 #include "profile.h"
@@ -102,7 +104,7 @@ __device__ __forceinline__ int panel_block_min(int v, int* red, int* out) {
 // All arithmetic is the same fraction-free step as in the plain loop:
 // row_i <- h row_i - f_i pivot with f_i kept in column cc.
 // Pivots of a panel from a window of its first w + WIN_EXTRA remaining rows,
-// one block, no grid-wide synchronisation.  Every column's pivot is the
+// without grid-wide synchronisation.  Every column's pivot is the
 // lowest-index remaining row with a nonzero entry (section 3.2: over a finite
 // field any nonzero entry serves, and the RREF does not depend on the choice),
 // and the window holds the lowest-index remaining rows: when it has a pivot in
@@ -111,92 +113,117 @@ __device__ __forceinline__ int panel_block_min(int v, int* red, int* out) {
 // grid-wide search in panel_kernel would find.  It then writes them (k, J,
 // Pi, panelU), advances panel_kernel's arrival counter by the w x G arrivals
 // that kernel would have made, and sets win_ok so that panel_kernel returns
-// at once; otherwise it leaves everything to panel_kernel.  Values are held in
-// Montgomery form, as in panel_kernel.
-__global__ void __launch_bounds__(WIN_THREADS)
+// at once; otherwise it leaves everything to panel_kernel.
+//
+// One cluster of WIN_CTAS blocks: block c holds window rows
+// [c WIN_ROWS_CTA, (c+1) WIN_ROWS_CTA) in its shared memory (Montgomery
+// form, as in panel_kernel).  Per column each block posts its lowest
+// candidate row, one cluster barrier makes the posts (and every block's
+// earlier row updates) visible, every block takes the minimum, reads the
+// pivot row from its owner's shared memory and eliminates its own rows.  A
+// post slot is reused two columns later, after another cluster barrier.
+__global__ void __cluster_dims__(WIN_CTAS, 1, 1) __launch_bounds__(WIN_THREADS)
 window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f, DenseState* st,
               uint32_t* __restrict__ panelU, int G) {
-    extern __shared__ __align__(16) uint32_t P[];   // rows x (w + 1)
-    __shared__ int red[2][WIN_THREADS / 32];
-    __shared__ unsigned char isp[NB_MAX + WIN_EXTRA];
-    __shared__ int own[NB_MAX], Jl[NB_MAX];
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ __align__(16) uint32_t P[WIN_ROWS_CTA * (NB_MAX + 1)];
+    __shared__ int post[2];
+    __shared__ int red[WIN_THREADS / 32];
+    __shared__ unsigned char isp[WIN_ROWS_CTA];
+    __shared__ int own[NB_MAX], Jc[NB_MAX];        // window row and panel column of pivot t
     constexpr int RG = WIN_THREADS / NB_MAX;        // row groups of the elimination
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = (int)cluster.block_rank();
     const int SW = w + 1;
     const int64_t r = st->r;
     const int64_t left = m - r > 0 ? m - r : 0;
     const int rows = (int)(left < w + WIN_EXTRA ? left : w + WIN_EXTRA);
-    for (int e = tid; e < rows * w; e += WIN_THREADS) {
+    const int g0 = c * WIN_ROWS_CTA;                                   // first window row of this block
+    const int lrows = max(0, min(WIN_ROWS_CTA, rows - g0));            // rows held here
+    for (int e = tid; e < lrows * w; e += WIN_THREADS) {
         const int i = e / w, j = e - i * w;
-        P[i * SW + j] = to_mont(M[(r + i) * ld + c0 + j], f);
+        P[i * SW + j] = to_mont(M[(r + g0 + i) * ld + c0 + j], f);
     }
-    for (int i = tid; i < rows; i += WIN_THREADS) isp[i] = 0;
+    for (int i = tid; i < WIN_ROWS_CTA; i += WIN_THREADS) isp[i] = 0;
     __syncthreads();
-    int kk = 0, buf = 0;
+    int kk = 0, par = 0;
     const int jj = tid % NB_MAX, rg = tid / NB_MAX;
     for (int cc = 0; cc < w; ++cc) {
-        // the lowest remaining window row with a nonzero entry in column cc
-        int c = (tid < rows && !isp[tid] && P[tid * SW + cc] != 0u) ? tid : INT_MAX;
-        c = __reduce_min_sync(0xffffffffu, c);
-        if (lane == 0) red[buf][warp] = c;
+        // this block's lowest remaining row with a nonzero entry in column cc
+        int cand = (tid < lrows && !isp[tid] && P[tid * SW + cc] != 0u) ? g0 + tid : INT_MAX;
+        cand = __reduce_min_sync(0xffffffffu, cand);
+        if (lane == 0) red[warp] = cand;
         __syncthreads();
+        if (tid == 0) {
+            int v = INT_MAX;
+#pragma unroll
+            for (int x = 0; x < WIN_THREADS / 32; ++x) v = min(v, red[x]);
+            post[par] = v;
+        }
+        cluster.sync();   // posts and every block's row updates of column cc - 1 are visible
         int q = INT_MAX;
 #pragma unroll
-        for (int x = 0; x < WIN_THREADS / 32; ++x) q = min(q, red[buf][x]);
-        buf ^= 1;
-        if (q == INT_MAX) continue;   // no pivot in this column (the same for every thread)
-        const uint32_t h = P[q * SW + cc];
+        for (int b = 0; b < WIN_CTAS; ++b) q = min(q, *cluster.map_shared_rank(&post[par], b));
+        par ^= 1;
+        if (q == INT_MAX) continue;   // no pivot in this column (the same in every block)
+        const int owner = q / WIN_ROWS_CTA, ql = q - owner * WIN_ROWS_CTA;
+        const uint32_t* prow = cluster.map_shared_rank(P, owner) + ql * SW;
+        const uint32_t h = prow[cc];
+        if (owner == c && tid == 0) isp[ql] = 1;
         if (tid == 0) {
-            isp[q] = 1;
             own[kk] = q;
-            Jl[kk] = cc;
+            Jc[kk] = cc;
         }
         ++kk;
-        // fraction-free elimination of column cc from the other remaining
-        // rows: row_i <- h row_i - f_i row_q on the columns right of cc
+        // fraction-free elimination of column cc from this block's other
+        // remaining rows: row_i <- h row_i - f_i row_q on the columns right of cc
         const int nc = w - cc - 1;
         if (jj < nc) {
-            // six independent rows per batch: all loads, then the products,
-            // then the stores, so the batch's latencies overlap
-            constexpr int U = 6;
+            constexpr int U = (WIN_ROWS_CTA + RG - 1) / RG;
             const int j = cc + 1 + jj;
-            const uint32_t pv = P[q * SW + j];
-            for (int i0 = rg; i0 < rows; i0 += U * RG) {
-                uint32_t fi[U], x[U];
+            const uint32_t pv = prow[j];
+            uint32_t fi[U], x[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int i = i0 + u * RG;
-                    const bool ok = i < rows && i != q && !isp[i];
-                    fi[u] = ok ? P[i * SW + cc] : 0u;
-                    x[u] = ok ? P[i * SW + j] : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (fi[u] != 0u) x[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (fi[u] != 0u) P[(i0 + u * RG) * SW + j] = x[u];
+            for (int u = 0; u < U; ++u) {
+                const int i = rg + u * RG;
+                const bool ok = i < lrows && g0 + i != q && !isp[i];
+                fi[u] = ok ? P[i * SW + cc] : 0u;
+                x[u] = ok ? P[i * SW + j] : 0u;
             }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (fi[u] != 0u) x[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (fi[u] != 0u) P[(rg + u * RG) * SW + j] = x[u];
         }
         __syncthreads();
     }
     if (kk == w || rows == left) {
         for (int t = tid; t < kk; t += WIN_THREADS) {
-            st->J[t] = c0 + Jl[t];
-            st->Pi[t] = (int32_t)(r + own[t]);
+            const int q = own[t];
+            if (q / WIN_ROWS_CTA != c) continue;
+            st->Pi[t] = (int32_t)(r + q);
         }
         for (int e = tid; e < kk * w; e += WIN_THREADS) {
             const int t = e / w, j = e - t * w;
-            panelU[(size_t)t * NB_MAX + j] = mont_redc(P[own[t] * SW + j], f);
+            const int q = own[t];
+            if (q / WIN_ROWS_CTA != c) continue;
+            panelU[(size_t)t * NB_MAX + j] = mont_redc(P[(q - g0) * SW + j], f);
         }
-        if (tid == 0) {
-            st->k = kk;
-            st->win_ok = 1;
-            atomicAdd(&st->bar.count, (unsigned)w * (unsigned)G);
+        if (c == 0) {
+            for (int t = tid; t < kk; t += WIN_THREADS) st->J[t] = c0 + Jc[t];
+            if (tid == 0) {
+                st->k = kk;
+                st->win_ok = 1;
+                atomicAdd(&st->bar.count, (unsigned)w * (unsigned)G);
+            }
         }
-    } else if (tid == 0) {
+    } else if (c == 0 && tid == 0) {
         st->win_ok = 0;
     }
+    cluster.sync();   // no block leaves while others may still read its shared memory
 }
 
 __global__ void __launch_bounds__(PANEL_THREADS)
@@ -673,8 +700,6 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
                                         (int)psmem));
     LINAC_CUDA_TRY(cudaFuncSetAttribute(einv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)EINV_SMEM));
-    LINAC_CUDA_TRY(cudaFuncSetAttribute(window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)WIN_SMEM));
     int occ = 0;
     LINAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_kernel, PANEL_THREADS, psmem));
     if (occ < 1 || G > occ * sm_count()) return LINAC_ERR_UNSUPPORTED;
@@ -705,7 +730,7 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
         const int64_t ncols = n - c0;
         {
             ProfScope ps(stream, PROF_PANEL);
-            window_kernel<<<1, WIN_THREADS, WIN_SMEM, stream>>>(dA, m, ld, (int)c0, w, f, st, panelU, G);
+            window_kernel<<<WIN_CTAS, WIN_THREADS, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, panelU, G);
         }
         {
             const uint32_t* Mc = dA;

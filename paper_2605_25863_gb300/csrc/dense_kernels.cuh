@@ -8,15 +8,16 @@
 namespace linac {
 
 constexpr int PANEL_THREADS = 512;   // block size of panel_kernel
-constexpr int WIN_THREADS = 1024;    // block size of window_kernel
 constexpr int WIN_EXTRA = 16;        // window rows beyond the panel width
-constexpr size_t WIN_SMEM = (size_t)(NB_MAX + WIN_EXTRA) * (NB_MAX + 1) * 4;
+constexpr int WIN_CTAS = 8;          // thread blocks of window_kernel's cluster
+constexpr int WIN_THREADS = 256;     // threads per block of window_kernel
+constexpr int WIN_ROWS_CTA = (NB_MAX + WIN_EXTRA + WIN_CTAS - 1) / WIN_CTAS;   // window rows per block
 constexpr int EINV_COLS = 8;         // columns of E = G^{-1} per einv_kernel block
 constexpr size_t EINV_SMEM = ((size_t)NB_MAX * (NB_MAX + 1) + (size_t)NB_MAX * EINV_COLS) * 4;
 
 __global__ void init_kernel(DenseState* st, int32_t* d_pivots, int64_t npiv, int32_t* d_rank);
 __global__ void finish_kernel(DenseState* st, int32_t* d_pivots, int32_t* d_rank);
-__global__ void __launch_bounds__(WIN_THREADS)
+__global__ void __cluster_dims__(WIN_CTAS, 1, 1) __launch_bounds__(WIN_THREADS)
 window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f, DenseState* st,
               uint32_t* __restrict__ panelU, int G);
 __global__ void __launch_bounds__(PANEL_THREADS)
