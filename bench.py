@@ -54,11 +54,11 @@ SM_MAX_MHZ = 2070.0       # GB300 maximum SM clock
 IMAD_WIDE_PER_SM_CLK = 32
 # DRAM bytes per output of update_plain_kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of the third panel of the
-# 8192 x 8448 elimination: 481.1 MB for 8192 x 8192 outputs; summary in
+# 8192 x 8448 elimination: 480.8 MB for 8192 x 8192 outputs; summary in
 # profiles/update_plain_rref_8192x8448.md), valid while the kernel's sources
 # hash to UPDATE_SRC_SHA; the traffic is reported as null otherwise
-UPDATE_BYTES_PER_OUTPUT = 481.1e6 / (8192 * 8192)
-UPDATE_SRC_SHA = "480f9cad0db8f1ef"
+UPDATE_BYTES_PER_OUTPUT = 480.8e6 / (8192 * 8192)
+UPDATE_SRC_SHA = "b220f7406c7ca3e3"
 UPDATE_SRC = ["paper_2605_25863_gb300/csrc/update_plain.cu", "paper_2605_25863_gb300/csrc/linac_device.cuh",
               "paper_2605_25863_gb300/csrc/update.cuh"]
 
