@@ -6,19 +6,23 @@
 // rank-1 update of every other row.  Here the same elimination is blocked by
 // panels of nb columns [c0, c1):
 //
-//   1. panel_kernel   (cooperative)  finds the k <= nb pivots of the panel
-//      among the rows not yet used (the current rank r .. m-1).  One grid
-//      barrier per column; the elimination inside the panel is fraction-free
-//      (row_i <- h * row_i - f_i * pivot_row), so no inverse is on this
-//      sequential path.  It records the pivot rows Pi, pivot columns J and,
-//      in place of the eliminated entries, the multipliers f.
+//   1. window_kernel  (one 8-block cluster) finds the k <= nb pivots of the
+//      panel among the first nb + 16 rows not yet used, by fraction-free
+//      elimination (row_i <- h * row_i - f_i * pivot_row, so no inverse is on
+//      this sequential path) with one cluster barrier per column.  When the
+//      window has a pivot in every column (or holds every remaining row) its
+//      result is exactly that of the full search; otherwise
+//      panel_kernel   (cooperative) searches every remaining row, one grid
+//      arrival per column.  Either records the pivot rows Pi, the pivot
+//      columns J and the pivot rows' fraction-free panel entries.
 //   2. gather_*       F = M[:, J] (the multipliers of the final update, in
 //      balanced signed form, stored transposed) and W = M[Pi, c0:n].
 //   3. heads_inverse  batched inverses of the k pivot heads (binary extended
 //      Euclid, one thread each).
-//   4. trsm_kernel    replays the panel's fraction-free recurrence on W,
-//      scales each row by its head's inverse and back-substitutes, giving
-//      the k reduced pivot rows R (identity at J).
+//   4. einv_kernel    replays the panel's fraction-free recurrence, the
+//      scaling by the heads' inverses and the back substitution on the
+//      identity, giving E = G^{-1} (G = M[Pi, J]); R = E W on the update
+//      kernel is the k reduced pivot rows (identity at J).
 //   5. move_kernel    rows of [r, r+k) that are not pivots move to the pivot
 //      rows' old places (the paper's row swap, done once per panel).
 //   6. update_plain   every row d outside [r, r+k):  M[d, c0:n] -= F[d] * R
