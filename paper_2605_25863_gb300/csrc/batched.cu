@@ -37,7 +37,7 @@ constexpr int BT_NBUCKETS = 5;         // m <= 64, 128, 256, 512, 1024
 // largest row count of bucket b: 64, 128, 256, 512, 1024
 __host__ __device__ constexpr int bt_bucket_max(int b) { return 64 << b; }
 constexpr int BT_FLAG_FALLBACK = 0x100;
-constexpr int BT_WINDOW = 16;         // rows of the pivot window beyond the panel width
+constexpr int BT_WINDOW = 8;          // rows of the pivot window beyond the panel width
 
 // The pivot window's slab: bt_win_rows rows of 2 NB + 1 words (NB panel
 // entries, NB coefficients over the pivot rows, one pad word against bank
