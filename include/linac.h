@@ -170,10 +170,13 @@ linac_status linac_solve_ex(const uint32_t *d_A, int64_t m, int64_t nA, int64_t 
  * thread block, largest first, in per-size-bucket persistent launches whose
  * panel widths come from linac_batched_tune (or defaults).  With
  * LINAC_SHARED_PATTERN, system 0 is the probe: its pivot rows and columns are
- * reused for every system of the same shape, and a system whose reused pivot
- * vanishes (or whose result leaves echelon form) is reduced again with the
- * search, starting from its partially reduced rows (row operations preserve
- * the RREF).
+ * reused for every system of the same shape reduced after them, and a system
+ * whose reused pivot vanishes (or whose result leaves echelon form) is reduced
+ * again with the search, starting from its partially reduced rows (row
+ * operations preserve the RREF).  For batches larger than four times the
+ * number of SMs the probe runs beside the first systems, which are reduced
+ * with the search until its pattern is published; smaller batches run the
+ * probe first.
  * Errors: as linac_rref; LINAC_ERR_UNSUPPORTED for sizes above the limits.
  */
 linac_status linac_rref_batched(uint32_t *d_data, const int64_t *d_offsets,

@@ -128,7 +128,7 @@ struct BtSmall {
     uint32_t hinv[NB], hs[NB];
     int red[BT_THREADS / 32];
     int red2[2][BT_THREADS / 32];
-    int s_min, s_sys, s_npairs, s_fail;
+    int s_min, s_sys, s_npairs, s_fail, s_pat;
 };
 
 // Block-wide minimum of one int per thread (INT_MAX = none).
@@ -740,10 +740,31 @@ batched_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ offsets,
                const int32_t* __restrict__ order, int blo, int bhi, Field f, int32_t* __restrict__ ranks,
                int32_t* __restrict__ pivots, const int64_t* __restrict__ piv_off, int32_t* __restrict__ sys_status,
                BatchScratch* bs, int pass, int use_pattern, const int32_t* pat_J, const int32_t* pat_Pi,
-               int32_t* fallback, BtFold fo) {
+               int32_t* fallback, BtFold fo, int probe) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ BtSmall<NB> sm;
     const BtLayout L = bt_layout(bt_bucket_max(bhi), NB);   // sized for the group's largest systems
+    if (probe && blockIdx.x == 0) {
+        // the probe: system 0 with the pivot search, recording its pattern,
+        // which is then published; the other blocks meanwhile reduce their
+        // systems with the search and take the pattern once it is there
+        const int m0 = dm[0], n0 = dn[0];
+        const int ns0 = dns ? min(dns[0], n0) : n0;
+        int rank0 = 0;
+        bt_reduce<NB, SH>(data + offsets[0], m0, n0, dld[0], ns0, f, fo, pivots + piv_off[0], &rank0, smem, L, sm, 0,
+                          nullptr, nullptr, nullptr, (int32_t*)pat_J, (int32_t*)pat_Pi, bs->pattern_k);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ranks[0] = rank0;
+            if (sys_status) sys_status[0] = 0;
+            bs->probe_m = m0;
+            bs->probe_n = n0;
+            bs->probe_ns = ns0;
+            __threadfence();   // the pattern and the probe's shape before the flag
+            atomicExch(&bs->pattern_ok, 1);
+        }
+        __syncthreads();
+    }
     int begin, end;
     if (pass == 0) {
         begin = bs->bbeg[bhi];
@@ -753,9 +774,18 @@ batched_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ offsets,
         end = bs->nfallback;
     }
     unsigned int* counter = &bs->counters[pass * BT_NBUCKETS + blo];
-    if (use_pattern && pass == 0 && !bs->pattern_ok) use_pattern = 0;
     for (;;) {
-        if (threadIdx.x == 0) sm.s_sys = (int)atomicAdd(counter, 1u);
+        if (threadIdx.x == 0) {
+            sm.s_sys = (int)atomicAdd(counter, 1u);
+            // the shared pattern, once the probe has published it (no waiting:
+            // a system pulled before that is reduced with the search)
+            int pat = 0;
+            if (use_pattern && pass == 0) {
+                pat = *(volatile int*)&bs->pattern_ok;
+                if (pat) __threadfence();   // the probe's pattern is visible after the flag
+            }
+            sm.s_pat = pat;
+        }
         __syncthreads();
         const int idx = begin + sm.s_sys;
         __syncthreads();
@@ -773,7 +803,7 @@ batched_kernel(uint32_t* __restrict__ data, const int64_t* __restrict__ offsets,
         bool ok = false;
         // the pattern applies only to systems shaped like the probe
         const bool same_shape = m == bs->probe_m && n == bs->probe_n && ns == bs->probe_ns;
-        const int mode = use_pattern && pass == 0 ? 1 : 0;
+        const int mode = sm.s_pat ? 1 : 0;
         // two call sites so that each is specialised for its mode
         if (mode == 1 && !same_shape) ok = false;
         else if (mode == 1)
@@ -891,7 +921,7 @@ static int bt_group_occupancy(int blo, int bhi, const BtWidths& wd, int sh, size
     return occ;
 }
 
-static linac_status launch_group(int blo, int bhi, int pass, int use_pattern, const BtWidths& wd,
+static linac_status launch_group(int blo, int bhi, int pass, int use_pattern, int probe, const BtWidths& wd,
                                  uint32_t* d_data, const int64_t* d_offsets, const int32_t* d_m, const int32_t* d_n,
                                  const int32_t* d_ld, const int32_t* d_nsearch, const int32_t* order,
                                  const Field& f, int32_t* d_ranks, int32_t* d_pivots, const int64_t* d_piv_offsets,
@@ -908,7 +938,7 @@ static linac_status launch_group(int blo, int bhi, int pass, int use_pattern, co
     Field fv = f;
     void* args[] = {&d_data, (void*)&d_offsets, (void*)&d_m, (void*)&d_n, (void*)&d_ld, (void*)&d_nsearch,
                     (void*)&order, &blo, &bhi, &fv, &d_ranks, &d_pivots, (void*)&d_piv_offsets, &d_status, &bs,
-                    &pass, &use_pattern, (void*)&pat_J, (void*)&pat_Pi, &fallback, &fo};
+                    &pass, &use_pattern, (void*)&pat_J, (void*)&pat_Pi, &fallback, &fo, &probe};
     ProfScope ps(stream, use_pattern ? PROF_PATTERN : PROF_BATCHED);
     LINAC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(BT_THREADS), args, smem, stream));
     return LINAC_OK;
@@ -973,7 +1003,14 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
     LINAC_CUDA_TRY(cudaMemsetAsync(&bs->pattern_ok, 0, sizeof(int), stream));
     int top = 0;
     while (top + 1 < BT_NBUCKETS && max_m > bt_bucket_max(top)) ++top;
-    if (pattern) {
+    // The probe: for batches of a few waves it runs in block 0 of the first
+    // persistent launch while the other blocks reduce with the search until
+    // its pattern is published; for smaller batches (which that launch would
+    // take up at once) it runs first, on its own, so every later system can
+    // use the pattern.
+    const bool inline_probe = pattern && batch > 4 * sm_count();
+    if (inline_probe) LINAC_CUDA_TRY(cudaMemsetAsync(bs->pattern_k, 0, sizeof(bs->pattern_k), stream));
+    if (pattern && !inline_probe) {
         // the probe runs with the widest panel the bucket of system 0 may need
         const int nb = bt_bucket_nb(top);
         const BtLayout L = bt_layout(bt_bucket_max(top), nb);
@@ -1008,7 +1045,9 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
         int glo[BT_NBUCKETS], ghi[BT_NBUCKETS];
         const int ng = bt_groups(top, wd, bt_fold_params(f).nshift, glo, ghi);
         for (int g = ng - 1; g >= 0; --g) {   // largest systems first
-            s = launch_group(glo[g], ghi[g], pass, pass == 0 && pattern ? 1 : 0, wd, d_data, d_offsets, d_m, d_n,
+            // the first launch of the pattern pass also runs the probe (its block 0)
+            const int probe = pass == 0 && inline_probe && g == ng - 1 ? 1 : 0;
+            s = launch_group(glo[g], ghi[g], pass, pass == 0 && pattern ? 1 : 0, probe, wd, d_data, d_offsets, d_m, d_n,
                              d_ld, d_nsearch, order, f, d_ranks, d_pivots, d_piv_offsets, d_status, bs, pat_J,
                              pat_Pi, fallback, stream);
             if (s != LINAC_OK) return s;
