@@ -61,12 +61,26 @@ def _load():
         lib.oracle_load_matrix.restype = ctypes.c_int
         lib.oracle_matmul.argtypes = [vp, i64, i64, i64, vp, i64, i64, u32, vp, i64]
         lib.oracle_matmul.restype = ctypes.c_int
+        u64 = ctypes.c_uint64
+        lib.oracle_rref64.argtypes = [vp, i64, i64, i64, u64, i64, ctypes.c_int, i32p, i32p]
+        lib.oracle_rref64.restype = ctypes.c_int
+        lib.oracle_solve64.argtypes = [vp, i64, i64, i64, i64, u64, ctypes.c_int, vp, i64, vp, i32p, i32p]
+        lib.oracle_solve64.restype = ctypes.c_int
+        lib.oracle_inverse64.argtypes = [u64, u64]
+        lib.oracle_inverse64.restype = u64
         _lib = lib
         return lib
 
 
 def _as_matrix(A) -> np.ndarray:
     A = np.ascontiguousarray(np.asarray(A, dtype=np.uint32))
+    if A.ndim != 2:
+        raise ValueError("expected a 2-D matrix")
+    return A
+
+
+def _as_matrix64(A) -> np.ndarray:
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.uint64))
     if A.ndim != 2:
         raise ValueError("expected a 2-D matrix")
     return A
@@ -218,3 +232,50 @@ def eval_template(points, coefs, monomials, mask, p: int) -> np.ndarray:
     out = np.zeros((count,) + mask.shape, dtype=np.uint32)
     out[:, mask] = vals
     return out
+
+
+# ---------------------------------------------------------------------------
+# 64-bit residues (paper section 2.3: uint64 storage for primes that do not
+# fit 32 bits, up to 2^64 - 1)
+
+def inverse64(h: int, p: int) -> int:
+    """h^(p-2) mod p for a 64-bit prime p (Fermat)."""
+    return int(_load().oracle_inverse64(int(h), int(p)))
+
+
+def rref64(A, p: int, col_limit: int | None = None, nthreads: int = 1):
+    """RREF over Z/pZ of a uint64 matrix, 3 <= p < 2^64 prime (section 3.2's
+    column loop with 128-bit products).  Returns (R, rank, pivots)."""
+    R = _as_matrix64(A).copy()
+    m, n = R.shape
+    if col_limit is None:
+        col_limit = n
+    piv = np.full(max(min(m, n), 1), -1, dtype=np.int32)
+    rank = ctypes.c_int32(0)
+    rc = _load().oracle_rref64(R.ctypes.data, m, n, n, p, col_limit, nthreads, ctypes.byref(rank),
+                               piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc != 0:
+        raise ValueError("oracle_rref64 rejected its arguments")
+    return R, int(rank.value), piv[: rank.value].copy()
+
+
+def solve64(A, B, p: int, nthreads: int = 1):
+    """Particular solution of A X = B over Z/pZ with uint64 residues
+    (section 5.2).  Returns (X, consistent, rank, pivots, reduced [A | B])."""
+    A = _as_matrix64(A)
+    B = _as_matrix64(B)
+    m, nA = A.shape
+    if B.shape[0] != m:
+        raise ValueError("A and B need the same number of rows")
+    k = B.shape[1]
+    M = np.ascontiguousarray(np.concatenate([A, B], axis=1))
+    X = np.zeros((max(nA, 1), max(k, 1)), dtype=np.uint64)
+    cons = np.zeros(max(k, 1), dtype=np.uint8)
+    piv = np.full(max(min(m, nA + k), 1), -1, dtype=np.int32)
+    rank = ctypes.c_int32(0)
+    rc = _load().oracle_solve64(M.ctypes.data, m, nA, k, nA + k, p, nthreads, X.ctypes.data, X.shape[1],
+                                cons.ctypes.data, ctypes.byref(rank),
+                                piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc != 0:
+        raise ValueError("oracle_solve64 rejected its arguments")
+    return (X[:nA, :k].copy(), cons[:k].astype(bool), int(rank.value), piv[: rank.value].copy(), M)

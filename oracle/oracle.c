@@ -22,7 +22,10 @@
  * Arithmetic: entries are canonical residues in [0, p), p an odd prime below
  * 2^31.  Every product is formed in uint64_t (< 2^62) and reduced with the C
  * '%' operator -- no Barrett, Montgomery, Shoup or limb tricks.  Inverses are
- * Fermat's h^(p-2) mod p by square-and-multiply.
+ * Fermat's h^(p-2) mod p by square-and-multiply.  The functions at the end of
+ * the file (oracle_rref64, oracle_solve64, oracle_inverse64) repeat the
+ * elimination for uint64 residues and primes below 2^64, with products in
+ * unsigned __int128; they are pinned in tests/test_oracle64_pins.py.
  *
  * Threads: the row updates of one pivot step are independent of one another;
  * with nthreads > 1 each thread owns a contiguous range of rows and the
@@ -272,6 +275,151 @@ int oracle_matmul(const uint32_t *A, int64_t m, int64_t K, int64_t lda,
                 s = (s + ((uint64_t)A[i * lda + k] * (uint64_t)B[k * ldb + j]) % p) % p;
             C[i * ldc + j] = (uint32_t)s;
         }
+    }
+    return 0;
+}
+
+/* ===========================================================================
+ * 64-bit residues.  Section 2.3 ("Basic Usage"): residues are held as uint64
+ * when p does not fit 32 bits, for primes up to 2^64 - 1 (and section 3.4,
+ * "Optimisations", reads them two at a time as ulonglong2).  The elimination
+ * below is the same column loop as oracle_rref (section 3.2: Looping,
+ * Pivoting with the lowest-index nonzero row, Conditional Rescale by the
+ * Fermat inverse, Row reduce over every other row, Increment counters); only
+ * the number type differs.  Every product is formed in unsigned __int128
+ * (below 2^128) and reduced with the C '%' operator.
+ * ======================================================================== */
+
+typedef unsigned __int128 o_u128;
+
+static uint64_t o64_mul(uint64_t a, uint64_t b, uint64_t p) {
+    return (uint64_t)(((o_u128)a * (o_u128)b) % p);
+}
+
+static uint64_t o64_pow(uint64_t h, uint64_t e, uint64_t p) {
+    uint64_t acc = 1 % p;
+    h %= p;
+    for (; e; e >>= 1) {
+        if (e & 1) acc = o64_mul(acc, h, p);
+        h = o64_mul(h, h, p);
+    }
+    return acc;
+}
+
+/* 1/h mod p = h^(p-2) mod p (Fermat), h != 0. */
+uint64_t oracle_inverse64(uint64_t h, uint64_t p) { return o64_pow(h, p - 2, p); }
+
+typedef struct {
+    uint64_t *A;
+    int64_t m, n, ld;
+    uint64_t p;
+    int64_t col_limit;
+    int nthreads;
+    pthread_barrier_t bar;
+    int64_t rank_now, col_now;   /* written by thread 0 between barriers */
+    int have_pivot, finished;
+    int32_t *pivots;
+} o64_ctx;
+
+typedef struct { o64_ctx *C; int tid; } o64_arg;
+
+/* Column col_now: the lowest row at or below rank_now with a nonzero entry
+ * becomes the pivot row; it is swapped into row rank_now and scaled by the
+ * inverse of its head. */
+static void o64_pivot(o64_ctx *C) {
+    const int64_t ld = C->ld, c = C->col_now, r = C->rank_now;
+    uint64_t *A = C->A;
+    int64_t q = r;
+    while (q < C->m && A[q * ld + c] == 0) q++;
+    C->have_pivot = q < C->m;
+    if (!C->have_pivot) return;
+    for (int64_t j = 0; q != r && j < C->n; j++) {
+        uint64_t t = A[q * ld + j];
+        A[q * ld + j] = A[r * ld + j];
+        A[r * ld + j] = t;
+    }
+    uint64_t hinv = oracle_inverse64(A[r * ld + c], C->p);
+    for (int64_t j = c; j < C->n; j++) A[r * ld + j] = o64_mul(A[r * ld + j], hinv, C->p);
+}
+
+/* Rows [lo, hi) other than the pivot row: row_i -= row_i[c] * pivot_row,
+ * written as row_i + (p - f) * pivot_row so every term stays unsigned. */
+static void o64_reduce_rows(o64_ctx *C, int64_t lo, int64_t hi) {
+    const int64_t ld = C->ld, c = C->col_now, prow = C->rank_now;
+    const uint64_t p = C->p;
+    uint64_t *A = C->A;
+    for (int64_t i = lo; i < hi; i++) {
+        uint64_t f = A[i * ld + c];
+        if (i == prow || f == 0) continue;
+        uint64_t minus_f = p - f;
+        for (int64_t j = c; j < C->n; j++) {
+            o_u128 v = (o_u128)A[i * ld + j] + (o_u128)minus_f * A[prow * ld + j];
+            A[i * ld + j] = (uint64_t)(v % p);
+        }
+    }
+}
+
+static void *o64_worker(void *argp) {
+    o64_arg *arg = (o64_arg *)argp;
+    o64_ctx *C = arg->C;
+    const int64_t lo = (C->m * arg->tid) / C->nthreads, hi = (C->m * (arg->tid + 1)) / C->nthreads;
+    for (;;) {
+        if (arg->tid == 0) {
+            C->finished = C->col_now >= C->col_limit || C->rank_now >= C->m;
+            if (!C->finished) o64_pivot(C);
+        }
+        pthread_barrier_wait(&C->bar);
+        if (C->finished) break;
+        if (C->have_pivot) o64_reduce_rows(C, lo, hi);
+        pthread_barrier_wait(&C->bar);
+        if (arg->tid == 0) {
+            if (C->have_pivot) C->pivots[C->rank_now++] = (int32_t)C->col_now;
+            C->col_now++;
+        }
+    }
+    return NULL;
+}
+
+/* In-place RREF of the m x n uint64 matrix A (leading dimension ld) over
+ * Z/pZ, 3 <= p < 2^64 prime, pivots searched in columns [0, col_limit).
+ * pivots[0..min(m,n)) gets the pivot columns, -1 after the rank.
+ * Returns 0, or -1 for bad arguments. */
+int oracle_rref64(uint64_t *A, int64_t m, int64_t n, int64_t ld, uint64_t p, int64_t col_limit,
+                  int nthreads, int32_t *rank, int32_t *pivots) {
+    if (m < 0 || n < 0 || ld < n || p < 3 || col_limit < 0 || col_limit > n) return -1;
+    nthreads = nthreads < 1 ? 1 : (nthreads > 256 ? 256 : nthreads);
+    for (int64_t i = 0; i < (m < n ? m : n); i++) pivots[i] = -1;
+    o64_ctx C;
+    memset(&C, 0, sizeof C);
+    C.A = A; C.m = m; C.n = n; C.ld = ld; C.p = p; C.col_limit = col_limit;
+    C.nthreads = nthreads; C.pivots = pivots;
+    pthread_barrier_init(&C.bar, NULL, (unsigned)nthreads);
+    o64_arg args[256];
+    pthread_t th[256];
+    for (int t = 0; t < nthreads; t++) { args[t].C = &C; args[t].tid = t; }
+    for (int t = 1; t < nthreads; t++) pthread_create(&th[t], NULL, o64_worker, &args[t]);
+    o64_worker(&args[0]);
+    for (int t = 1; t < nthreads; t++) pthread_join(th[t], NULL);
+    pthread_barrier_destroy(&C.bar);
+    *rank = (int32_t)C.rank_now;
+    return 0;
+}
+
+/* Section 5.2 with uint64 residues: reduce M = [A | B] with pivots in A's
+ * nA columns; column j of B is consistent iff its reduced entries vanish at
+ * and below the rank; X[pivots[t]][j] = reduced B[t][j], free variables and
+ * inconsistent columns zero. */
+int oracle_solve64(uint64_t *M, int64_t m, int64_t nA, int64_t k, int64_t ld, uint64_t p, int nthreads,
+                   uint64_t *X, int64_t ldx, uint8_t *consistent, int32_t *rank, int32_t *pivots) {
+    if (k < 0 || ldx < k) return -1;
+    if (oracle_rref64(M, m, nA + k, ld, p, nA, nthreads, rank, pivots)) return -1;
+    for (int64_t i = 0; i < nA * ldx; i++) X[i] = 0;
+    for (int64_t j = 0; j < k; j++) {
+        int64_t i = *rank;
+        while (i < m && M[i * ld + nA + j] == 0) i++;
+        consistent[j] = (uint8_t)(i == m);
+        for (int64_t t = 0; consistent[j] && t < *rank; t++)
+            X[pivots[t] * ldx + j] = M[t * ld + nA + j];
     }
     return 0;
 }

@@ -84,6 +84,46 @@ def uniform(shape, p: int, key: int, start: int = 0) -> np.ndarray:
     return out.reshape(shape)
 
 
+def uniform64(shape, p: int, key: int, start: int = 0) -> np.ndarray:
+    """Residues in [0, p) (uint64) for a modulus up to 2^64 - 1, filling
+    ``shape`` in row-major order: floor(w * p / 2^64) of each 64-bit word w of
+    the stream (multiply-shift; the 128-bit product is assembled from 32-bit
+    halves so numpy's uint64 never overflows)."""
+    count = int(np.prod(shape))
+    out = np.empty(count, dtype=np.uint64)
+    lo32 = np.uint64(0xFFFFFFFF)
+    s32 = np.uint64(32)
+    ph, pl = np.uint64(p >> 32), np.uint64(p & 0xFFFFFFFF)
+    chunk = 1 << 22
+    for s in range(0, count, chunk):
+        w = words(key, min(chunk, count - s), start + s)
+        wh, wl = w >> s32, w & lo32
+        hh, hl, lh, ll = wh * ph, wh * pl, wl * ph, wl * pl       # each < 2^64
+        mid = (hl & lo32) + (lh & lo32) + (ll >> s32)              # < 3 * 2^32
+        out[s:s + len(w)] = hh + (hl >> s32) + (lh >> s32) + (mid >> s32)
+    return out.reshape(shape)
+
+
+def rank_deficient64(m: int, n: int, d: int, p: int, seed: int = 2, terms: int = 8):
+    """uint64 counterpart of ``rank_deficient`` for a prime up to 2^64 - 1:
+    m x n uniform, ``d`` seeded rows replaced by random combinations of
+    ``terms`` other rows (exact Python-integer arithmetic).  Returns
+    (M, replaced_rows)."""
+    M = uniform64((m, n), p, stream_key(seed, "rank_deficient64"))
+    perm = np.argsort(words(stream_key(seed, "rd64_rows"), m))
+    targets = np.sort(perm[:d])
+    pool = np.setdiff1d(np.arange(m), targets)
+    pick = words(stream_key(seed, "rd64_pick"), max(d * terms, 1), 0)
+    coefs = uniform64((max(d, 1), terms), p, stream_key(seed, "rd64_coef"))
+    for a, t in enumerate(targets):
+        acc = np.zeros(n, dtype=object)
+        for b in range(terms):
+            src = int(pool[int(pick[a * terms + b] % np.uint64(len(pool)))])
+            acc = (acc + M[src].astype(object) * max(int(coefs[a, b]), 1)) % p
+        M[t] = np.asarray(acc, dtype=np.uint64) if n else M[t]
+    return M, targets
+
+
 def unit_floats(key: int, count: int, start: int = 0) -> np.ndarray:
     """Uniform doubles in [0, 1) from the top 53 bits (input construction only)."""
     w = words(key, count, start)

@@ -40,11 +40,29 @@ CONSTRUCTION_MUTANTS = {
                                 "for (int64_t k = 1; k < K; k++)\n                s = (s"),
 }
 
+# planted slips in the 64-bit elimination, caught by its own pins
+MUTANTS64 = {
+    "o64_row_swap_dropped": ("for (int64_t j = 0; q != r && j < C->n; j++) {",
+                             "for (int64_t j = 0; 0 && j < C->n; j++) {"),
+    "o64_product_wraps_at_64_bits": ("(o_u128)minus_f * A[prow * ld + j];",
+                                     "(o_u128)(minus_f * A[prow * ld + j]);"),
+    "o64_update_skips_rows_above": ("if (i == prow || f == 0) continue;", "if (i <= prow || f == 0) continue;"),
+    "o64_wrong_inverse_exponent": ("return o64_pow(h, p - 2, p);", "return o64_pow(h, p - 3, p);"),
+    "o64_solution_read_into_wrong_row": ("X[pivots[t] * ldx + j] = M[t * ld + nA + j];",
+                                         "X[t * ldx + j] = M[t * ld + nA + j];"),
+    "o64_square_reduced_at_64_bits": ("return (uint64_t)(((o_u128)a * (o_u128)b) % p);",
+                                      "return (uint64_t)((a * b) % p);"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(CONSTRUCTION_MUTANTS))
+PIN_FILES = {**{k: "test_oracle_pins.py" for k in MUTANTS},
+             **{k: "test_oracle_construction.py" for k in CONSTRUCTION_MUTANTS},
+             **{k: "test_oracle64_pins.py" for k in MUTANTS64}}
+
+
+@pytest.mark.parametrize("name", sorted(PIN_FILES))
 def test_pins_fail_on_mutant(name, tmp_path):
-    before, after = MUTANTS[name] if name in MUTANTS else CONSTRUCTION_MUTANTS[name]
-    pins = "test_oracle_pins.py" if name in MUTANTS else "test_oracle_construction.py"
+    before, after = {**MUTANTS, **CONSTRUCTION_MUTANTS, **MUTANTS64}[name]
+    pins = PIN_FILES[name]
     src = open(SRC).read()
     assert src.count(before) == 1, f"mutation site for {name} not found exactly once"
     mut = tmp_path / "oracle_mut.c"
