@@ -45,7 +45,7 @@ typedef struct CUstream_st *cudaStream_t;
 typedef enum {
     LINAC_OK = 0,
     LINAC_ERR_ARG = 1,        /* bad shape, null pointer, bad option */
-    LINAC_ERR_PRIME = 2,      /* p is not an odd prime below 2^31 */
+    LINAC_ERR_PRIME = 2,      /* p is not an odd prime below 2^31 (below 2^64: *64 entry points) */
     LINAC_ERR_ALIGN = 3,      /* ld not a multiple of 4, or pointer not 16-byte aligned */
     LINAC_ERR_CUDA = 4,       /* a CUDA runtime call failed */
     LINAC_ERR_NOMEM = 5,      /* scratch allocation failed */
@@ -286,6 +286,46 @@ linac_status linac_rank_factor(const uint32_t *d_A, int64_t m, int64_t n, int64_
 
 /* Scratch bytes linac_rref_ex needs for an m x n problem with these options
  * (the library allocates them itself; exposed for capacity planning). */
+/*
+ * uint64 residues: primes that do not fit 32 bits.  Section 2.3 ("Basic
+ * Usage") selects uint64 storage for 2^32 - 1 < p <= 2^64 - 1; these entry
+ * points accept every odd prime 3 <= p < 2^64 (so small primes can be
+ * checked against the uint32 entry points).  Conventions as above, except:
+ *   - matrices hold uint64_t residues in [0, p); the leading dimension is a
+ *     multiple of 2 elements and the matrix starts 16-byte aligned (rows are
+ *     read two residues at a time, section 3.4 "Optimisations");
+ *   - the elimination is the same blocked Gauss-Jordan (section 3.2) with
+ *     32-column panels, Montgomery arithmetic modulo 2^64 and exact 160-bit
+ *     accumulation in the trailing update; the panel's pivots come from a
+ *     window of the first 48 remaining rows, or from a search over all
+ *     remaining rows when the window lacks one;
+ *   - scratch: (32 (m + n) + 32 m) * 8 bytes plus a few KB, per stream
+ *     (linac_workspace64_bytes), allocated on first use as for linac_rref;
+ *   - no tensor-core path: the options' path and nb must be 0.
+ */
+
+/* In-place RREF of the m x n uint64 matrix (same outputs as linac_rref). */
+linac_status linac_rref64(uint64_t *d_A, int64_t m, int64_t n, int64_t ld, uint64_t p,
+                          int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
+
+/* linac_rref64 with a pivot-search limit [0, ncols_search) and options
+ * (NULL = defaults; only `validate` may be set: it checks every entry is
+ * below p first and sets the device status word to LINAC_ERR_RANGE). */
+linac_status linac_rref64_ex(uint64_t *d_A, int64_t m, int64_t n, int64_t ld, uint64_t p,
+                             int64_t ncols_search, int32_t *d_rank, int32_t *d_pivots,
+                             const linac_options *opts, cudaStream_t stream);
+
+/* Particular solutions of A X = B with uint64 residues (section 5.2); same
+ * arguments and results as linac_solve.  [A | B] is reduced in library
+ * scratch (m * (nA + k) * 8 bytes); A and B are not modified. */
+linac_status linac_solve64(const uint64_t *d_A, int64_t m, int64_t nA, int64_t ldA,
+                           const uint64_t *d_B, int64_t k, int64_t ldB, uint64_t p,
+                           uint64_t *d_X, int64_t ldX, uint8_t *d_consistent,
+                           int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
+
+/* Scratch bytes linac_rref64 uses for an m x n matrix (0 for negative sizes). */
+size_t linac_workspace64_bytes(int64_t m, int64_t n);
+
 size_t linac_workspace_bytes(int64_t m, int64_t n, const linac_options *opts);
 
 /* Status word written by device-side checks of the most recent call on this

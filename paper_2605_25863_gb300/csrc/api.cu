@@ -77,6 +77,43 @@ Field make_field(uint32_t p) {
     return f;
 }
 
+bool is_prime_u64(uint64_t n) {
+    if (n < 2) return false;
+    static const uint64_t bases[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    for (uint64_t q : bases) {
+        if (n == q) return true;
+        if (n % q == 0) return false;
+    }
+    uint64_t d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) { d >>= 1; ++s; }
+    for (uint64_t a : bases) {
+        uint64_t x = powmod64_host(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool composite = true;
+        for (int i = 1; i < s; ++i) {
+            x = mulmod64_host(x, x, n);
+            if (x == n - 1) { composite = false; break; }
+        }
+        if (composite) return false;
+    }
+    return true;
+}
+
+Field64 make_field64(uint64_t p) {
+    Field64 f;
+    f.p = p;
+    // p^(-1) mod 2^64 by Newton's iteration: p is its own inverse mod 8 (3
+    // bits) and each step doubles the correct low bits (3, 6, 12, 24, 48, 96)
+    uint64_t inv = p;
+    for (int i = 0; i < 5; ++i) inv *= 2ull - p * inv;
+    f.pinv = 0ull - inv;
+    f.r1 = (0ull - p) % p;                 // 2^64 - p is congruent to 2^64
+    f.r2 = mulmod64_host(f.r1, f.r1, p);   // 2^128 mod p
+    f.r3 = mulmod64_host(f.r2, f.r1, p);   // 2^192 mod p
+    return f;
+}
+
 int fold_shifts(const Field& f, FoldShifts* fs) {
     uint32_t c = f.c32;
     int n = 0;
@@ -185,6 +222,15 @@ linac_status check_matrix(const void* d, int64_t m, int64_t n, int64_t ld) {
     if (m < 0 || n < 0 || ld < n || m > INT32_MAX || n > INT32_MAX) return LINAC_ERR_ARG;
     if (m > 0 && n > 0 && !d) return LINAC_ERR_ARG;
     if (ld % 4 != 0 || ((uintptr_t)d % 16) != 0) return LINAC_ERR_ALIGN;
+    return LINAC_OK;
+}
+
+// uint64 matrices: ld a multiple of 2 elements (16-byte rows, section 3.4's
+// ulonglong2 accesses) and a 16-byte aligned start.
+linac_status check_matrix64(const void* d, int64_t m, int64_t n, int64_t ld) {
+    if (m < 0 || n < 0 || ld < n || m > INT32_MAX || n > INT32_MAX) return LINAC_ERR_ARG;
+    if (m > 0 && n > 0 && !d) return LINAC_ERR_ARG;
+    if (ld % 2 != 0 || ((uintptr_t)d % 16) != 0) return LINAC_ERR_ALIGN;
     return LINAC_OK;
 }
 
@@ -308,6 +354,54 @@ linac_status linac_batched_panel_widths(int32_t* nb_out) {
     return LINAC_OK;
 }
 
+linac_status linac_rref64_ex(uint64_t* d_A, int64_t m, int64_t n, int64_t ld, uint64_t p, int64_t ncols_search,
+                             int32_t* d_rank, int32_t* d_pivots, const linac_options* opts, cudaStream_t stream) {
+    linac_status s = check_matrix64(d_A, m, n, ld);
+    if (s != LINAC_OK) return s;
+    if (ncols_search < 0 || ncols_search > n || !d_rank) return LINAC_ERR_ARG;
+    if (std::min(m, ncols_search) > 0 && !d_pivots) return LINAC_ERR_ARG;
+    if (opts && (opts->path != LINAC_PATH_AUTO || opts->nb != 0)) return LINAC_ERR_ARG;
+    if (!prime64_ok(p)) return LINAC_ERR_PRIME;
+    if ((s = reset_status(stream)) != LINAC_OK) return s;
+    if (opts && opts->validate) {
+        s = validate64_range(d_A, m, n, ld, p, status_word(stream), stream);
+        if (s != LINAC_OK) return s;
+    }
+    return dense64_rref(d_A, m, n, ld, make_field64(p), ncols_search, d_rank, d_pivots, stream);
+}
+
+linac_status linac_rref64(uint64_t* d_A, int64_t m, int64_t n, int64_t ld, uint64_t p, int32_t* d_rank,
+                          int32_t* d_pivots, cudaStream_t stream) {
+    return linac_rref64_ex(d_A, m, n, ld, p, n, d_rank, d_pivots, nullptr, stream);
+}
+
+linac_status linac_solve64(const uint64_t* d_A, int64_t m, int64_t nA, int64_t ldA, const uint64_t* d_B, int64_t k,
+                           int64_t ldB, uint64_t p, uint64_t* d_X, int64_t ldX, uint8_t* d_consistent,
+                           int32_t* d_rank, int32_t* d_pivots, cudaStream_t stream) {
+    linac_status s = check_matrix64(d_A, m, nA, ldA);
+    if (s != LINAC_OK) return s;
+    if ((s = check_matrix64(d_B, m, k, ldB)) != LINAC_OK) return s;
+    if (ldX < k || !d_rank || (std::min(m, nA) > 0 && !d_pivots)) return LINAC_ERR_ARG;
+    if (k > 0 && nA > 0 && !d_X) return LINAC_ERR_ARG;
+    if (k > 0 && !d_consistent) return LINAC_ERR_ARG;
+    if (nA + k > INT32_MAX) return LINAC_ERR_ARG;
+    if (!prime64_ok(p)) return LINAC_ERR_PRIME;
+    if ((s = reset_status(stream)) != LINAC_OK) return s;
+    const int64_t ldM = (int64_t)align_up((size_t)std::max<int64_t>(nA + k, 1), 2);
+    void* buf = nullptr;
+    if ((s = scratch_get_slot(stream, 5, (size_t)std::max<int64_t>(m, 1) * ldM * 8, &buf)) != LINAC_OK) return s;
+    uint64_t* dM = (uint64_t*)buf;
+    if ((s = solve64_pack(d_A, m, nA, ldA, d_B, k, ldB, dM, ldM, stream)) != LINAC_OK) return s;
+    s = dense64_rref(dM, m, nA + k, ldM, make_field64(p), nA, d_rank, d_pivots, stream);
+    if (s != LINAC_OK) return s;
+    return solve64_extract(dM, m, nA, k, ldM, d_rank, d_pivots, d_X, ldX, d_consistent, stream);
+}
+
+size_t linac_workspace64_bytes(int64_t m, int64_t n) {
+    if (m < 0 || n < 0) return 0;
+    return dense64_workspace_bytes(m, n);
+}
+
 size_t linac_workspace_bytes(int64_t m, int64_t n, const linac_options* opts) {
     if (m < 0 || n < 0) return 0;
     const int nb = opts && opts->nb ? opts->nb : dense_default_nb(m, n);
@@ -327,7 +421,7 @@ const char* linac_status_string(linac_status s) {
     switch (s) {
         case LINAC_OK: return "ok";
         case LINAC_ERR_ARG: return "invalid argument";
-        case LINAC_ERR_PRIME: return "p is not an odd prime below 2^31";
+        case LINAC_ERR_PRIME: return "p is not an odd prime in the entry point's range";
         case LINAC_ERR_ALIGN: return "leading dimension or pointer misaligned";
         case LINAC_ERR_CUDA: return "CUDA runtime error";
         case LINAC_ERR_NOMEM: return "out of device memory";

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/linac.h"
+#include "field64.cuh"
 #include "linac_device.cuh"
 
 namespace linac {
@@ -30,7 +31,8 @@ inline bool prime_ok(uint32_t p) { return p >= 3 && p < (1u << 31) && is_prime_u
 // (device, stream); growing synchronises the stream first.
 linac_status scratch_get(cudaStream_t stream, size_t bytes, void** ptr);
 // Same, for an independent buffer `slot` (0 = dense elimination, 1 = solve's
-// augmented matrix, 2 = batched driver, 3 = limb planes).
+// augmented matrix, 2 = batched driver, 3 = limb planes, 4 = uint64
+// elimination, 5 = the uint64 solve's augmented matrix).
 linac_status scratch_get_slot(cudaStream_t stream, int slot, size_t bytes, void** ptr);
 
 // Device status word of the most recent call on this (device, stream): lives
@@ -83,5 +85,24 @@ linac_status batched_rref(uint32_t* d_data, const int64_t* d_offsets, const int3
 linac_status batched_tune(const Field& f, int32_t* nb_out, cudaStream_t stream);
 void batched_get_nb(int32_t* nb_out);
 linac_status batched_set_nb(const int32_t* nb);
+
+// uint64 residues, primes below 2^64 (dense64.cu; constants and the prime
+// test in api.cu).
+Field64 make_field64(uint64_t p);
+// Deterministic Miller-Rabin for 64-bit n with the first twelve primes as
+// bases (no strong pseudoprime to all of them below 3.3e24; Sorenson and
+// Webster 2015).
+bool is_prime_u64(uint64_t n);
+inline bool prime64_ok(uint64_t p) { return p >= 3 && (p & 1) && is_prime_u64(p); }
+linac_status dense64_rref(uint64_t* dA, int64_t m, int64_t n, int64_t ld, const Field64& f, int64_t nsearch,
+                          int32_t* d_rank, int32_t* d_pivots, cudaStream_t stream);
+size_t dense64_workspace_bytes(int64_t m, int64_t n);
+linac_status solve64_pack(const uint64_t* dA, int64_t m, int64_t nA, int64_t ldA, const uint64_t* dB, int64_t k,
+                          int64_t ldB, uint64_t* dM, int64_t ldM, cudaStream_t stream);
+linac_status solve64_extract(const uint64_t* dM, int64_t m, int64_t nA, int64_t k, int64_t ldM,
+                             const int32_t* d_rank, const int32_t* d_pivots, uint64_t* dX, int64_t ldX,
+                             uint8_t* d_consistent, cudaStream_t stream);
+linac_status validate64_range(const uint64_t* dA, int64_t m, int64_t n, int64_t ld, uint64_t p, int* d_status,
+                              cudaStream_t stream);
 
 }  // namespace linac

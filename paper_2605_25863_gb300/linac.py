@@ -97,9 +97,16 @@ def lib():
         L.linac_matmul.argtypes = [vp, i64, i64, i64, vp, i64, i64, u32, vp, i64, vp]
         L.linac_null_space.argtypes = [vp, i64, i64, i64, vp, vp, u32, vp, i64, i64, vp, vp, vp]
         L.linac_rank_factor.argtypes = [vp, i64, i64, i64, vp, vp, vp, i64, i64, vp]
+        u64 = ctypes.c_uint64
+        L.linac_rref64.argtypes = [vp, i64, i64, i64, u64, vp, vp, vp]
+        L.linac_rref64_ex.argtypes = [vp, i64, i64, i64, u64, i64, vp, vp, ctypes.POINTER(Options), vp]
+        L.linac_solve64.argtypes = [vp, i64, i64, i64, vp, i64, i64, u64, vp, i64, vp, vp, vp, vp]
+        L.linac_workspace64_bytes.argtypes = [i64, i64]
+        L.linac_workspace64_bytes.restype = ctypes.c_size_t
         for name in ("linac_rref", "linac_rref_ex", "linac_solve", "linac_solve_ex",
                      "linac_rref_batched", "linac_last_device_status", "linac_version",
-                     "linac_load_matrix", "linac_matmul", "linac_null_space", "linac_rank_factor"):
+                     "linac_load_matrix", "linac_matmul", "linac_null_space", "linac_rank_factor",
+                     "linac_rref64", "linac_rref64_ex", "linac_solve64"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -358,3 +365,70 @@ def linac_batched_panel_widths() -> list[int]:
     out = (ctypes.c_int32 * 5)()
     _check(lib().linac_batched_panel_widths(out), "linac_batched_panel_widths")
     return list(out)
+
+
+# ---------------------------------------------------------------------------
+# uint64 residues (primes below 2^64; paper section 2.3).  Device matrices are
+# 2-D int64 (or uint64) tensors holding the residues' bit patterns, row stride
+# a multiple of 2 elements.
+
+def _matrix64(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or t.dim() != 2 or not t.is_cuda:
+        raise ValueError(f"{name} must be a 2-D CUDA tensor")
+    if t.dtype != torch.int64 and str(t.dtype) != "torch.uint64":
+        raise ValueError(f"{name} must be int64 or uint64")
+    if t.stride(1) != 1 and t.shape[1] > 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+    ld = t.stride(0) if t.shape[0] > 1 else max(t.shape[1] + t.shape[1] % 2, 2)
+    return t.data_ptr(), t.shape[0], t.shape[1], ld
+
+
+def padded64(rows: int, cols: int, device="cuda") -> torch.Tensor:
+    """A zeroed rows x cols int64 view whose row stride is a multiple of 2."""
+    ld = max(cols + cols % 2, 2)
+    return torch.zeros((rows, ld), dtype=torch.int64, device=device)[:, :cols]
+
+
+def to_device64(M, device="cuda") -> torch.Tensor:
+    """Copy a host matrix of uint64 residues into a padded int64 device view."""
+    import numpy as np
+    M = np.ascontiguousarray(np.asarray(M, dtype=np.uint64))
+    out = padded64(M.shape[0], M.shape[1], device)
+    out.copy_(torch.from_numpy(M.view(np.int64)))
+    return out
+
+
+def host64(t: torch.Tensor):
+    """A device int64 matrix back on the host as uint64 residues."""
+    import numpy as np
+    return t.cpu().numpy().view(np.uint64)
+
+
+def linac_rref64(A: torch.Tensor, p: int, *, ncols_search: int | None = None, validate: bool = False,
+                 stream=None):
+    """In-place RREF of a uint64 matrix over Z/pZ, p an odd prime below 2^64.
+    Returns (rank, pivots) as int32 CUDA tensors."""
+    ptr, m, n, ld = _matrix64(A, "A")
+    ns = n if ncols_search is None else int(ncols_search)
+    rank = torch.zeros(1, dtype=torch.int32, device=A.device)
+    piv = torch.full((max(min(m, ns), 1),), -1, dtype=torch.int32, device=A.device)
+    o = _opts("auto", 0, validate)
+    _check(lib().linac_rref64_ex(ptr, m, n, ld, int(p), ns, rank.data_ptr(), piv.data_ptr(), ctypes.byref(o),
+                                 _stream_ptr(stream)), "linac_rref64")
+    return rank, piv[:min(m, ns)]
+
+
+def linac_solve64(A: torch.Tensor, B: torch.Tensor, p: int, *, stream=None):
+    """Particular solutions of A X = B with uint64 residues (section 5.2).
+    Returns (X, consistent, rank, pivots); A and B are not modified."""
+    pa, m, nA, ldA = _matrix64(A, "A")
+    pb, mb, k, ldB = _matrix64(B, "B")
+    if mb != m:
+        raise ValueError("A and B need the same number of rows")
+    X = torch.zeros((max(nA, 1), max(k, 1)), dtype=torch.int64, device=A.device)
+    cons = torch.zeros(max(k, 1), dtype=torch.uint8, device=A.device)
+    rank = torch.zeros(1, dtype=torch.int32, device=A.device)
+    piv = torch.full((max(min(m, nA), 1),), -1, dtype=torch.int32, device=A.device)
+    _check(lib().linac_solve64(pa, m, nA, ldA, pb, k, ldB, int(p), X.data_ptr(), X.stride(0), cons.data_ptr(),
+                               rank.data_ptr(), piv.data_ptr(), _stream_ptr(stream)), "linac_solve64")
+    return X[:nA, :k], cons[:k].bool(), rank, piv[:min(m, nA)]

@@ -92,3 +92,38 @@ def test_construction_and_derived_entry_points_check_arguments(lib):
     # rank factor: ld < n, ldC < ccols
     assert lib.linac_rank_factor(fake, 3, 4, 3, fake, fake, fake, 3, 4, None) == 1
     assert lib.linac_rank_factor(fake, 3, 4, 4, fake, fake, fake, 3, 2, None) == 1
+
+
+# composites a weak 64-bit prime test would pass: Carmichael numbers, strong
+# pseudoprimes to the bases 2..23 (3825123056546413051) and to 2, 3, 5, 7
+# (3215031751), even numbers, 2^64 - 1, and the Fermat number 2^32 + 1
+@pytest.mark.parametrize("p", [0, 1, 2, 4, 9, 561, 3215031751, 3825123056546413051, 2**32 + 1, 2**63,
+                               2**64 - 1, 2**61 + 1, (2**31 - 1) * (2**31 + 11)])
+def test_uint64_entry_points_reject_composites(lib, p):
+    rank = ctypes.c_int32()
+    piv = (ctypes.c_int32 * 4)()
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.linac_rref64(None, 0, 0, 2, p, ctypes.byref(rank), piv, None) == 2
+    assert lib.linac_solve64(fake, 4, 4, 4, fake, 2, 2, p, fake, 2, fake, ctypes.byref(rank), piv, None) == 2
+
+
+def test_uint64_entry_points_check_shapes_alignment_and_options(lib):
+    rank = ctypes.c_int32()
+    piv = (ctypes.c_int32 * 8)()
+    fake = ctypes.c_void_p(0x1000)
+    P = 2**64 - 59
+    assert lib.linac_rref64(fake, 4, 5, 5, P, ctypes.byref(rank), piv, None) == 3       # odd ld
+    assert lib.linac_rref64(ctypes.c_void_p(0x1008), 4, 4, 4, P, ctypes.byref(rank), piv, None) == 3
+    assert lib.linac_rref64(fake, -1, 4, 4, P, ctypes.byref(rank), piv, None) == 1
+    assert lib.linac_rref64(fake, 4, 6, 4, P, ctypes.byref(rank), piv, None) == 1       # ld < n
+    assert lib.linac_rref64(fake, 4, 4, 4, P, None, piv, None) == 1
+    assert lib.linac_rref64_ex(fake, 4, 4, 4, P, 5, ctypes.byref(rank), piv, None, None) == 1
+    for path, nb in ((1, 0), (2, 0), (0, 32)):
+        o = linac.Options(path, nb, 0, 0)
+        assert lib.linac_rref64_ex(fake, 4, 4, 4, P, 4, ctypes.byref(rank), piv, ctypes.byref(o), None) == 1
+    cons = ctypes.c_void_p(0x2000)
+    assert lib.linac_solve64(fake, 4, 4, 4, fake, 2, 2, P, fake, 1, cons, ctypes.byref(rank), piv, None) == 1
+    assert lib.linac_solve64(fake, 4, 4, 4, fake, 2, 2, P, fake, 2, None, ctypes.byref(rank), piv, None) == 1
+    assert lib.linac_solve64(fake, 4, 4, 5, fake, 2, 2, P, fake, 2, cons, ctypes.byref(rank), piv, None) == 3
+    assert lib.linac_workspace64_bytes(-1, 4) == 0
+    assert lib.linac_workspace64_bytes(100, 200) >= (32 * (128 + 256) + 32 * 100) * 8
