@@ -20,9 +20,14 @@
 //      old places at or after r+k, R goes to rows r..r+k-1.
 //   6. advance64_kernel: pivot list, r += k.
 // No block ever waits on another block; all state is device-resident, so
-// the host issues a fixed sequence of launches per panel.
+// the host issues a fixed sequence of launches per panel.  Panel kernels run
+// on a second stream, each overlapping the previous panel's update (see
+// dense64_rref).
 #include <algorithm>
 #include <climits>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "field64.cuh"
 #include "linac_host.h"
@@ -37,16 +42,25 @@ constexpr int P64_WARPS = P64_THREADS / 32;
 constexpr int P64_ROWS_PER_WARP = (W64_ROWS + P64_WARPS - 1) / P64_WARPS;
 constexpr int G64_BM = 64, G64_BN = 64, G64_THREADS = 256;
 
-struct Dense64State {
-    int32_t r;                 // rank so far
-    int32_t k;                 // pivots of the current panel
+// What one panel found.  Two of these alternate, so a panel kernel can run
+// while the previous panel's update still reads its own.
+struct Panel64Out {
+    int32_t k;                 // pivots of the panel
+    int32_t r0;                // rank before the panel = first row the pivot rows move to
     int32_t nmove;             // rows displaced by the move
-    int32_t tall_panels;       // panels that needed the full-height search
+    int32_t pad;
     int32_t pc[NB64];          // pivot columns (absolute), increasing
     int32_t pr[NB64];          // pivot rows (absolute, before the move), same order
-    int32_t mv_src[NB64];      // displaced rows (in [r, r+k))
-    int32_t mv_dst[NB64];      // their new places (old pivot rows at or after r+k)
+    int32_t mv_src[NB64];      // displaced rows (in [r0, r0+k))
+    int32_t mv_dst[NB64];      // their new places (old pivot rows at or after r0+k)
     uint64_t Et[NB64 * NB64];  // Et[s * NB64 + t] = E[t][s] * 2^128 mod p
+};
+
+struct Dense64State {
+    int32_t r;                 // rank so far (advanced once a panel's first 64 columns are final)
+    int32_t tall_panels;       // panels that needed the full-height search
+    int32_t pad[2];
+    Panel64Out out[2];
 };
 
 // ---------------------------------------------------------------------------
@@ -215,13 +229,13 @@ __device__ int tall_search64(const uint64_t* __restrict__ A, int64_t m, int64_t 
 
 __global__ void __launch_bounds__(P64_THREADS)
 panel64_kernel(const uint64_t* __restrict__ A, int64_t m, int64_t ld, int c0, int w, Field64 f,
-               Dense64State* __restrict__ st, uint64_t* __restrict__ tall) {
+               Dense64State* __restrict__ st, Panel64Out* __restrict__ po, uint64_t* __restrict__ tall) {
     __shared__ Panel64Smem sm;
     const int tid = threadIdx.x;
     const int r = st->r;
     const int64_t mrem = m - r;
     if (mrem <= 0 || w <= 0) {
-        if (tid == 0) { st->k = 0; st->nmove = 0; }
+        if (tid == 0) { po->k = 0; po->nmove = 0; po->r0 = r; }
         return;
     }
     int nrows = mrem < W64_ROWS ? (int)mrem : W64_ROWS;
@@ -247,15 +261,15 @@ panel64_kernel(const uint64_t* __restrict__ A, int64_t m, int64_t ld, int c0, in
     __syncthreads();
     const int lane = tid & 31, warp = tid >> 5;
     for (int s = warp; s < kk; s += P64_WARPS)
-        if (lane < kk) st->Et[s * NB64 + lane] = m64_mul(sm.T[sm.pslot[lane]][s], sm.dinv[lane], f);
+        if (lane < kk) po->Et[s * NB64 + lane] = m64_mul(sm.T[sm.pslot[lane]][s], sm.dinv[lane], f);
     if (warp == 0) {
         // rows r..r+kk-1 receive the pivot rows (lane t: pivot t, position
         // r+t); the non-pivot rows there go to the places the pivot rows leave
         // at or after r+kk, paired in order by two ballots
         const int prow = lane < kk ? sm.rowid[sm.pslot[lane]] : -1;
         if (lane < kk) {
-            st->pc[lane] = c0 + sm.pcl[lane];
-            st->pr[lane] = prow;
+            po->pc[lane] = c0 + sm.pcl[lane];
+            po->pr[lane] = prow;
         }
         sm.ispos[lane] = 0;
         __syncwarp();
@@ -265,11 +279,12 @@ panel64_kernel(const uint64_t* __restrict__ A, int64_t m, int64_t ld, int c0, in
         const bool vacated = lane < kk && prow >= r + kk;
         const unsigned bd = __ballot_sync(0xffffffffu, displaced), bv = __ballot_sync(0xffffffffu, vacated);
         const unsigned below = (1u << lane) - 1u;
-        if (displaced) st->mv_src[__popc(bd & below)] = r + lane;
-        if (vacated) st->mv_dst[__popc(bv & below)] = prow;
+        if (displaced) po->mv_src[__popc(bd & below)] = r + lane;
+        if (vacated) po->mv_dst[__popc(bv & below)] = prow;
         if (lane == 0) {
-            st->nmove = __popc(bd);   // equal to __popc(bv): both count the pivot rows outside [r, r+kk)
-            st->k = kk;
+            po->nmove = __popc(bd);   // equal to __popc(bv): both count the pivot rows outside [r, r+kk)
+            po->r0 = r;
+            po->k = kk;
         }
     }
 }
@@ -279,12 +294,12 @@ panel64_kernel(const uint64_t* __restrict__ A, int64_t m, int64_t ld, int c0, in
 // are zero.
 
 __global__ void __launch_bounds__(256)
-gather64_kernel(const uint64_t* __restrict__ A, int64_t m, int64_t ld, const Dense64State* __restrict__ st,
+gather64_kernel(const uint64_t* __restrict__ A, int64_t m, int64_t ld, const Panel64Out* __restrict__ po,
                 Field64 f, uint64_t* __restrict__ Ft, int64_t ldF) {
     __shared__ int32_t pcs[NB64];
-    const int k = st->k;
+    const int k = po->k;
     if (k == 0) return;
-    if (threadIdx.x < k) pcs[threadIdx.x] = st->pc[threadIdx.x];
+    if (threadIdx.x < k) pcs[threadIdx.x] = po->pc[threadIdx.x];
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ldF; i += (int64_t)gridDim.x * blockDim.x) {
         for (int s = 0; s < k; ++s) {
@@ -296,7 +311,7 @@ gather64_kernel(const uint64_t* __restrict__ A, int64_t m, int64_t ld, const Den
 
 // ---------------------------------------------------------------------------
 // C (rows x ncols) = sum_s At[s][i] B[s][j] / 2^128 mod p (ASSIGN), or
-// C -= that (update).  k = st->k <= NB64 products per output, accumulated
+// C -= that (update).  k = po->k <= NB64 products per output, accumulated
 // exactly in 160 bits.  Rows of B are B + brow[s] * ldB (brow = null: s).
 // ASSIGN takes rows = k (the pivot rows).  64 x 64 tile per 256-thread
 // block; each thread owns 4 rows x (2 + 2) columns, the columns split so
@@ -306,10 +321,10 @@ template <bool ASSIGN>
 __global__ void __launch_bounds__(G64_THREADS, 2)
 gemm64_kernel(const uint64_t* __restrict__ At, int64_t ldAt, const uint64_t* __restrict__ B, int64_t ldB,
               const int32_t* __restrict__ brow, uint64_t* __restrict__ C, int64_t ldC, int64_t nrows,
-              int64_t ncols, const Dense64State* __restrict__ st, Field64 f) {
+              int64_t ncols, const Panel64Out* __restrict__ po, Field64 f) {
     __shared__ __align__(16) uint64_t As[NB64][G64_BM];
     __shared__ __align__(16) uint64_t Bs[NB64][G64_BN];
-    const int k = st->k;
+    const int k = po->k;
     if (k == 0) return;
     const int64_t rows = ASSIGN ? (int64_t)k : nrows;
     const int64_t i0 = (int64_t)blockIdx.y * G64_BM, j0 = (int64_t)blockIdx.x * G64_BN;
@@ -381,34 +396,34 @@ gemm64_kernel(const uint64_t* __restrict__ At, int64_t ldAt, const uint64_t* __r
 // ---------------------------------------------------------------------------
 // Move, advance, init
 
+// Columns [c0 + j0, c0 + j1): the displaced rows go to the pivot rows' old
+// places, then R (columns relative to c0) fills rows r0..r0+k-1.
 __global__ void __launch_bounds__(256)
-move64_kernel(uint64_t* __restrict__ A, int64_t ld, int64_t ncols, int c0, const Dense64State* __restrict__ st,
-              const uint64_t* __restrict__ R, int64_t ldR) {
+move64_kernel(uint64_t* __restrict__ A, int64_t ld, int c0, int64_t j0, int64_t j1,
+              const Panel64Out* __restrict__ po, const uint64_t* __restrict__ R, int64_t ldR) {
     __shared__ int32_t src[NB64], dst[NB64];
-    const int k = st->k;
+    const int k = po->k;
     if (k == 0) return;
-    const int r = st->r, nm = st->nmove;
+    const int r = po->r0, nm = po->nmove;
     if (threadIdx.x < nm) {
-        src[threadIdx.x] = st->mv_src[threadIdx.x];
-        dst[threadIdx.x] = st->mv_dst[threadIdx.x];
+        src[threadIdx.x] = po->mv_src[threadIdx.x];
+        dst[threadIdx.x] = po->mv_dst[threadIdx.x];
     }
     __syncthreads();
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ncols; j += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t j = j0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < j1; j += (int64_t)gridDim.x * blockDim.x) {
         uint64_t* col = A + c0 + j;
         for (int u = 0; u < nm; ++u) col[(int64_t)dst[u] * ld] = col[(int64_t)src[u] * ld];
         for (int t = 0; t < k; ++t) col[(int64_t)(r + t) * ld] = R[(int64_t)t * ldR + j];
     }
 }
 
-__global__ void advance64_kernel(Dense64State* __restrict__ st, int32_t* __restrict__ pivots,
-                                 int32_t* __restrict__ d_rank) {
-    const int k = st->k, r = st->r;
-    if ((int)threadIdx.x < k) pivots[r + threadIdx.x] = st->pc[threadIdx.x];
-    __syncthreads();
+// Pivot list and rank; the panel's record stays for its remaining columns.
+__global__ void advance64_kernel(Dense64State* __restrict__ st, const Panel64Out* __restrict__ po,
+                                 int32_t* __restrict__ pivots, int32_t* __restrict__ d_rank) {
+    const int k = po->k, r = po->r0;
+    if ((int)threadIdx.x < k) pivots[r + threadIdx.x] = po->pc[threadIdx.x];
     if (threadIdx.x == 0) {
         st->r = r + k;
-        st->k = 0;
-        st->nmove = 0;
         *d_rank = r + k;
     }
 }
@@ -419,9 +434,12 @@ __global__ void init64_kernel(Dense64State* __restrict__ st, int32_t* __restrict
         pivots[i] = -1;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->r = 0;
-        st->k = 0;
-        st->nmove = 0;
         st->tall_panels = 0;
+        for (int b = 0; b < 2; ++b) {
+            st->out[b].k = 0;
+            st->out[b].nmove = 0;
+            st->out[b].r0 = 0;
+        }
         *d_rank = 0;
     }
 }
@@ -491,7 +509,7 @@ Dense64Layout dense64_layout(int64_t m, int64_t n) {
     size_t o = 0;
     L.off_state = o; o = align_up(o + sizeof(Dense64State), 256);
     L.ldF = (int64_t)align_up((size_t)std::max<int64_t>(m, 1), G64_BM);
-    L.off_ft = o;    o = align_up(o + (size_t)NB64 * L.ldF * 8, 256);
+    L.off_ft = o;    o = align_up(o + (size_t)2 * NB64 * L.ldF * 8, 256);   // two F buffers
     L.ldR = (int64_t)align_up((size_t)std::max<int64_t>(n, 1), G64_BN);
     L.off_r = o;     o = align_up(o + (size_t)NB64 * L.ldR * 8, 256);
     L.off_tall = o;  o = align_up(o + (size_t)std::max<int64_t>(m, 1) * NB64 * 8, 256);
@@ -499,10 +517,49 @@ Dense64Layout dense64_layout(int64_t m, int64_t n) {
     return L;
 }
 
+// Second stream (highest priority) and events of one caller stream: the
+// panel kernels run on `side` so that each overlaps the previous panel's
+// update.  Created on first
+// use per (device, stream) and kept for the life of the process.
+struct Side64 {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, panel = nullptr, narrow = nullptr;
+};
+std::mutex g_side_mu;
+std::map<std::pair<int, cudaStream_t>, Side64> g_side;
+
+linac_status side64_get(cudaStream_t stream, Side64* out) {
+    int dev = 0;
+    LINAC_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    Side64& sd = g_side[std::make_pair(dev, stream)];
+    if (!sd.side) {
+        // highest priority: when an update block retires, the block scheduler
+        // places the waiting panel block first instead of another update block
+        int least = 0, greatest = 0;
+        LINAC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        LINAC_CUDA_TRY(cudaStreamCreateWithPriority(&sd.side, cudaStreamNonBlocking, greatest));
+        LINAC_CUDA_TRY(cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming));
+        LINAC_CUDA_TRY(cudaEventCreateWithFlags(&sd.panel, cudaEventDisableTiming));
+        LINAC_CUDA_TRY(cudaEventCreateWithFlags(&sd.narrow, cudaEventDisableTiming));
+    }
+    *out = sd;
+    return LINAC_OK;
+}
+
 }  // namespace
 
 size_t dense64_workspace_bytes(int64_t m, int64_t n) { return dense64_layout(m, n).total; }
 
+// Per panel t (record out[t & 1], F buffer t & 1):
+//   side:   [wait: panel t-1's first 64 columns final] panel kernel, gather F
+//   stream: [wait: panel t] R = E W; update and move of the panel's first 64
+//           columns (its own 32 and the next panel's 32); advance the rank
+//           [signal]; update and move of the remaining columns.
+// So panel t+1 runs while panel t's remaining columns are updated.  The next
+// R = E W waits for that update (stream order), the next gather writes the
+// other F buffer, and the next panel writes the other record; each buffer's
+// previous reader finished before the signal the writer waits for.
 linac_status dense64_rref(uint64_t* dA, int64_t m, int64_t n, int64_t ld, const Field64& f, int64_t nsearch,
                           int32_t* d_rank, int32_t* d_pivots, cudaStream_t stream) {
     const int64_t npiv = std::min(m, nsearch);
@@ -511,9 +568,11 @@ linac_status dense64_rref(uint64_t* dA, int64_t m, int64_t n, int64_t ld, const 
     void* base = nullptr;
     linac_status s = scratch_get_slot(stream, 4, L.total, &base);
     if (s != LINAC_OK) return s;
+    Side64 sd;
+    if ((s = side64_get(stream, &sd)) != LINAC_OK) return s;
     char* ws = (char*)base;
     Dense64State* st = (Dense64State*)(ws + L.off_state);
-    uint64_t* Ft = (uint64_t*)(ws + L.off_ft);
+    uint64_t* Ft2[2] = {(uint64_t*)(ws + L.off_ft), (uint64_t*)(ws + L.off_ft) + (size_t)NB64 * L.ldF};
     uint64_t* R = (uint64_t*)(ws + L.off_r);
     uint64_t* tall = (uint64_t*)(ws + L.off_tall);
     {
@@ -522,39 +581,62 @@ linac_status dense64_rref(uint64_t* dA, int64_t m, int64_t n, int64_t ld, const 
         init64_kernel<<<blocks, 256, 0, stream>>>(st, d_pivots, npiv, d_rank);
         LINAC_CUDA_TRY(cudaGetLastError());
     }
-    if (m == 0 || n == 0) return LINAC_OK;
+    if (m == 0 || n == 0 || nsearch == 0) return LINAC_OK;   // no panel: nothing forks to the side stream
     const unsigned gather_blocks = (unsigned)std::min<int64_t>((L.ldF + 255) / 256, 1024);
-    for (int64_t c0 = 0; c0 < nsearch; c0 += NB64) {
+    const unsigned gy = (unsigned)((m + G64_BM - 1) / G64_BM);
+    LINAC_CUDA_TRY(cudaEventRecord(sd.fork, stream));
+    LINAC_CUDA_TRY(cudaStreamWaitEvent(sd.side, sd.fork, 0));
+    int t = 0;
+    for (int64_t c0 = 0; c0 < nsearch; c0 += NB64, ++t) {
         const int w = (int)std::min<int64_t>(NB64, nsearch - c0);
         const int64_t ncols = n - c0;
-        const unsigned gx = (unsigned)((ncols + G64_BN - 1) / G64_BN);
+        const int64_t nnarrow = std::min<int64_t>(ncols, G64_BN);
+        Panel64Out* po = &st->out[t & 1];
+        uint64_t* Ft = Ft2[t & 1];
+        if (t > 0) LINAC_CUDA_TRY(cudaStreamWaitEvent(sd.side, sd.narrow, 0));
         {
-            ProfScope ps(stream, PROF_U64_PANEL);
-            panel64_kernel<<<1, P64_THREADS, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, tall);
+            ProfScope ps(sd.side, PROF_U64_PANEL);
+            panel64_kernel<<<1, P64_THREADS, 0, sd.side>>>(dA, m, ld, (int)c0, w, f, st, po, tall);
         }
         {
-            ProfScope ps(stream, PROF_GATHER_F);
-            gather64_kernel<<<gather_blocks, 256, 0, stream>>>(dA, m, ld, st, f, Ft, L.ldF);
+            ProfScope ps(sd.side, PROF_GATHER_F);
+            gather64_kernel<<<gather_blocks, 256, 0, sd.side>>>(dA, m, ld, po, f, Ft, L.ldF);
         }
+        LINAC_CUDA_TRY(cudaEventRecord(sd.panel, sd.side));
+        LINAC_CUDA_TRY(cudaStreamWaitEvent(stream, sd.panel, 0));
         {
             ProfScope ps(stream, PROF_TRSM);
-            gemm64_kernel<true><<<dim3(gx, 1), G64_THREADS, 0, stream>>>(st->Et, NB64, dA + c0, ld, st->pr, R, L.ldR,
-                                                                         NB64, ncols, st, f);
+            const unsigned gx = (unsigned)((ncols + G64_BN - 1) / G64_BN);
+            gemm64_kernel<true><<<dim3(gx, 1), G64_THREADS, 0, stream>>>(po->Et, NB64, dA + c0, ld, po->pr, R,
+                                                                         L.ldR, NB64, ncols, po, f);
         }
         {
             ProfScope ps(stream, PROF_U64_UPDATE);
-            const unsigned gy = (unsigned)((m + G64_BM - 1) / G64_BM);
-            gemm64_kernel<false><<<dim3(gx, gy), G64_THREADS, 0, stream>>>(Ft, L.ldF, R, L.ldR, nullptr, dA + c0, ld,
-                                                                           m, ncols, st, f);
+            gemm64_kernel<false><<<dim3(1, gy), G64_THREADS, 0, stream>>>(Ft, L.ldF, R, L.ldR, nullptr, dA + c0, ld,
+                                                                          m, nnarrow, po, f);
         }
         {
             ProfScope ps(stream, PROF_MOVE);
-            const unsigned mb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncols + 255) / 256, 1024));
-            move64_kernel<<<mb, 256, 0, stream>>>(dA, ld, ncols, (int)c0, st, R, L.ldR);
+            move64_kernel<<<1, 256, 0, stream>>>(dA, ld, (int)c0, 0, nnarrow, po, R, L.ldR);
         }
         {
             ProfScope ps(stream, PROF_FINISH);
-            advance64_kernel<<<1, NB64, 0, stream>>>(st, d_pivots, d_rank);
+            advance64_kernel<<<1, NB64, 0, stream>>>(st, po, d_pivots, d_rank);
+        }
+        LINAC_CUDA_TRY(cudaEventRecord(sd.narrow, stream));
+        if (ncols > nnarrow) {
+            const int64_t nrest = ncols - nnarrow;
+            {
+                ProfScope ps(stream, PROF_U64_UPDATE);
+                const unsigned gx = (unsigned)((nrest + G64_BN - 1) / G64_BN);
+                gemm64_kernel<false><<<dim3(gx, gy), G64_THREADS, 0, stream>>>(
+                    Ft, L.ldF, R + nnarrow, L.ldR, nullptr, dA + c0 + nnarrow, ld, m, nrest, po, f);
+            }
+            {
+                ProfScope ps(stream, PROF_MOVE);
+                const unsigned mb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nrest + 255) / 256, 1024));
+                move64_kernel<<<mb, 256, 0, stream>>>(dA, ld, (int)c0, nnarrow, ncols, po, R, L.ldR);
+            }
         }
         LINAC_CUDA_TRY(cudaGetLastError());
     }

@@ -12,7 +12,8 @@ against the CPU oracle, bit for bit:
 * for primes below 2^31, the uint64 path agrees with the uint32 path;
 * 1024 x 1056 against the oracle, and at 4096 x 4097 the identity block and
   A x = b on sampled rows checked with Python integers;
-* the range validation option.
+* the range validation option, and a capture into a CUDA graph (the panel
+  kernels run on a second stream forked from the caller's).
 """
 import os
 
@@ -147,3 +148,28 @@ def test_validate_flags_entries_not_below_p():
     linac.linac_rref64(A, p, validate=True)
     torch.cuda.synchronize()
     assert linac.linac_last_device_status() == 7
+
+
+def test_rref64_captured_in_a_cuda_graph():
+    """The panel kernels run on a second stream forked from the caller's;
+    the fork and join must hold inside a CUDA graph capture too."""
+    p = 2**61 - 1
+    M, _ = synth.rank_deficient64(200, 230, 7, p, seed=8)
+    R0, r0, piv0 = oracle.rref64(M, p, nthreads=NTH)
+    src = linac.to_device64(M)
+    A = src.clone()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        linac.linac_rref64(A, p)        # uncaptured call on this stream: scratch exists
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rank, piv = linac.linac_rref64(A, p)
+    for _ in range(2):
+        A.copy_(src)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(rank.item()) == r0
+        assert np.array_equal(piv.cpu().numpy()[:r0], piv0)
+        assert np.array_equal(linac.host64(A), R0)
