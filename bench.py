@@ -77,8 +77,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU oracle, path comparison and batched legs")
     ap.add_argument("--batch-count", type=int, default=10000)
-    ap.add_argument("--only", choices=["all", "batched", "construction"], default="all",
+    ap.add_argument("--only", choices=["all", "batched", "construction", "dense64"], default="all",
                     help="batched / construction: run that workload alone (a profiling aid; prints its own line)")
+    ap.add_argument("--m64", type=int, default=8192, help="unknowns of the uint64 leg's system")
     ap.add_argument("--widths", default="",
                     help="comma-separated panel widths per size bucket for the batched legs (default: autotune)")
     ap.add_argument("--measure-peaks", action="store_true",
@@ -294,6 +295,9 @@ def run_ours(args):
     if args.only == "construction":
         print(json.dumps({"construction": construction_leg(args, linac, synth, dev)}), flush=True)
         return 0
+    if args.only == "dense64":
+        print(json.dumps({"dense64": dense64_leg(args, linac, synth, dev)}), flush=True)
+        return 0
 
     m, rhs = args.m, args.rhs
     n = m + rhs
@@ -393,6 +397,7 @@ def run_ours(args):
         line["batched"] = batched_leg(args, linac, synth, dev, stream)
         line["shared_pattern"] = shared_leg(args, linac, synth, dev, stream)
         line["construction"] = construction_leg(args, linac, synth, dev)
+        line["dense64"] = dense64_leg(args, linac, synth, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -563,6 +568,44 @@ def shared_leg(args, linac, synth, dev, stream):
     out["panel_widths"] = widths
     out["launch"] = "cuda_graph"
     return out
+
+
+def dense64_leg(args, linac, synth, dev):
+    """uint64 residues (paper section 2.3: primes that do not fit 32 bits):
+    RREF of [A | B], A m64 x m64 uniform (default 8192), 256 right-hand sides,
+    p = 2^64 - 59 (the largest prime below 2^64).  The default input (577 MB)
+    is larger than L2 and is restored from a pristine copy outside the timed
+    region.  Checked: rank m64, pivots 0..m64-1, and A X = B on sampled
+    entries in exact integers."""
+    import torch
+    p = 2**64 - 59
+    m, rhs = args.m64, 256
+    n = m + rhs
+    M = synth.uniform64((m, n), p, synth.stream_key(64, "dense64"))
+    pristine = linac.to_device64(M)
+    A = pristine.clone()
+    times = []
+    for it in range(4):
+        A.copy_(pristine)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rank, piv = linac.linac_rref64(A, p)
+        e1.record()
+        torch.cuda.synchronize()
+        if it:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    R = linac.host64(A)
+    ok = int(rank.item()) == m and np.array_equal(piv.cpu().numpy(), np.arange(m))
+    for i, c in ((0, 0), (m // 2 + 1, 131), (m - 1, rhs - 1)):
+        row = [int(v) for v in M[i, :m]]
+        x = [int(v) for v in R[:m, m + c]]
+        ok = ok and sum(a * b for a, b in zip(row, x)) % p == int(M[i, m + c])
+    W = sum((m - 1) * (n - t - 1) for t in range(m))
+    return {"workload": f"RREF {m} x {n} ({rhs} RHS), p = 2^64 - 59, uint64", "ms": ms,
+            "value": W / (ms / 1e3), "unit": "field MAC/s", "correct": bool(ok), "timed_runs": len(times)}
 
 
 def construction_leg(args, linac, synth, dev):
