@@ -299,8 +299,12 @@ linac_status linac_rank_factor(const uint32_t *d_A, int64_t m, int64_t n, int64_
  *     accumulation in the trailing update; the panel's pivots come from a
  *     window of the first 48 remaining rows, or from a search over all
  *     remaining rows when the window lacks one;
- *   - scratch: (32 (m + n) + 32 m) * 8 bytes plus a few KB, per stream
+ *   - scratch: 32 (3 m + n) * 8 bytes plus a few KB, per stream
  *     (linac_workspace64_bytes), allocated on first use as for linac_rref;
+ *   - the panel kernels run on a second, highest-priority stream that the
+ *     library creates on first use per (device, stream) and forks from and
+ *     joins back to `stream` with events; as with scratch memory, make one
+ *     uncaptured call on a stream before capturing calls on it;
  *   - no tensor-core path: the options' path and nb must be 0.
  */
 
