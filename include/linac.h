@@ -327,6 +327,17 @@ linac_status linac_solve64(const uint64_t *d_A, int64_t m, int64_t nA, int64_t l
                            uint64_t *d_X, int64_t ldX, uint8_t *d_consistent,
                            int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
 
+/* linac_null_space and linac_rank_factor (section 5.1) for uint64 residues:
+ * same arguments, outputs and errors, with uint64 matrices (d_R, d_K, d_A,
+ * d_C) and p an odd prime below 2^64 (the free columns' -1 is p - 1). */
+linac_status linac_null_space64(const uint64_t *d_R, int64_t m, int64_t n, int64_t ld,
+                                const int32_t *d_rank, const int32_t *d_pivots, uint64_t p,
+                                uint64_t *d_K, int64_t kcols, int64_t ldK, int32_t *d_free,
+                                int32_t *d_nullity, cudaStream_t stream);
+linac_status linac_rank_factor64(const uint64_t *d_A, int64_t m, int64_t n, int64_t ld,
+                                 const int32_t *d_rank, const int32_t *d_pivots,
+                                 uint64_t *d_C, int64_t ccols, int64_t ldC, cudaStream_t stream);
+
 /* Scratch bytes linac_rref64 uses for an m x n matrix (0 for negative sizes). */
 size_t linac_workspace64_bytes(int64_t m, int64_t n);
 

@@ -279,3 +279,24 @@ def solve64(A, B, p: int, nthreads: int = 1):
     if rc != 0:
         raise ValueError("oracle_solve64 rejected its arguments")
     return (X[:nA, :k].copy(), cons[:k].astype(bool), int(rank.value), piv[: rank.value].copy(), M)
+
+
+def null_space64(R, pivots, p: int) -> np.ndarray:
+    """Canonical null-space basis of a uint64 RREF (section 5.1): for the q-th
+    free column f, -1 (that is, p - 1) in row f and R[t][f] in row pivots[t]."""
+    R = _as_matrix64(R)
+    n = R.shape[1]
+    piv = [int(c) for c in pivots]
+    free = [c for c in range(n) if c not in set(piv)]
+    K = np.zeros((n, len(free)), dtype=np.uint64)
+    for q, f in enumerate(free):
+        K[f, q] = p - 1
+        for t, c in enumerate(piv):
+            K[c, q] = R[t, f]
+    return K
+
+
+def rank_factor64(A, pivots) -> np.ndarray:
+    """C = A[:, J] for uint64 residues (section 5.1: A = C R)."""
+    A = _as_matrix64(A)
+    return np.ascontiguousarray(A[:, np.asarray(pivots, dtype=np.int64)])

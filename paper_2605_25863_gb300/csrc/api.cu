@@ -389,7 +389,7 @@ linac_status linac_solve64(const uint64_t* d_A, int64_t m, int64_t nA, int64_t l
     if ((s = reset_status(stream)) != LINAC_OK) return s;
     const int64_t ldM = (int64_t)align_up((size_t)std::max<int64_t>(nA + k, 1), 2);
     void* buf = nullptr;
-    if ((s = scratch_get_slot(stream, 5, (size_t)std::max<int64_t>(m, 1) * ldM * 8, &buf)) != LINAC_OK) return s;
+    if ((s = scratch_get_slot(stream, 7, (size_t)std::max<int64_t>(m, 1) * ldM * 8, &buf)) != LINAC_OK) return s;
     uint64_t* dM = (uint64_t*)buf;
     if ((s = solve64_pack(d_A, m, nA, ldA, d_B, k, ldB, dM, ldM, stream)) != LINAC_OK) return s;
     s = dense64_rref(dM, m, nA + k, ldM, make_field64(p), nA, d_rank, d_pivots, stream);

@@ -566,7 +566,7 @@ linac_status dense64_rref(uint64_t* dA, int64_t m, int64_t n, int64_t ld, const 
     if ((m + G64_BM - 1) / G64_BM > 65535) return LINAC_ERR_UNSUPPORTED;
     const Dense64Layout L = dense64_layout(m, n);
     void* base = nullptr;
-    linac_status s = scratch_get_slot(stream, 4, L.total, &base);
+    linac_status s = scratch_get_slot(stream, 6, L.total, &base);
     if (s != LINAC_OK) return s;
     Side64 sd;
     if ((s = side64_get(stream, &sd)) != LINAC_OK) return s;

@@ -211,17 +211,18 @@ free_columns_kernel(const int32_t* __restrict__ rank_p, const int32_t* __restric
 
 // K[i][q] for q < kcols: -1 (= p - 1) at i = free[q], R[t][free[q]] at the
 // pivot column i = J[t], 0 elsewhere and in columns q >= nullity.
-__global__ void null_space_kernel(const uint32_t* __restrict__ R, int64_t ldr, int64_t n, const int32_t* __restrict__ pos,
-                                  const int32_t* __restrict__ free_c, const int32_t* __restrict__ nullity_p, uint32_t p,
-                                  uint32_t* __restrict__ K, int64_t kcols, int64_t ldk, int64_t i0) {
+template <typename T>
+__global__ void null_space_kernel(const T* __restrict__ R, int64_t ldr, int64_t n, const int32_t* __restrict__ pos,
+                                  const int32_t* __restrict__ free_c, const int32_t* __restrict__ nullity_p, T p,
+                                  T* __restrict__ K, int64_t kcols, int64_t ldk, int64_t i0) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = i0 + blockIdx.y;
     if (q >= kcols) return;
     const int nullity = *nullity_p;
-    uint32_t v = 0u;
+    T v = 0;
     if (q < nullity) {
         const int fc = free_c[q];
-        if (i == fc) v = p - 1u;
+        if (i == fc) v = p - 1;
         else {
             const int t = pos[i];
             if (t >= 0) v = R[(int64_t)t * ldr + fc];
@@ -231,14 +232,15 @@ __global__ void null_space_kernel(const uint32_t* __restrict__ R, int64_t ldr, i
 }
 
 // C[i][t] = A[i][J[t]] for t < rank, 0 for rank <= t < ccols.
-__global__ void rank_factor_kernel(const uint32_t* __restrict__ A, int64_t lda, int64_t n, const int32_t* __restrict__ rank_p,
-                                   const int32_t* __restrict__ piv, int64_t npiv_cap, uint32_t* __restrict__ C,
+template <typename T>
+__global__ void rank_factor_kernel(const T* __restrict__ A, int64_t lda, int64_t n, const int32_t* __restrict__ rank_p,
+                                   const int32_t* __restrict__ piv, int64_t npiv_cap, T* __restrict__ C,
                                    int64_t ccols, int64_t ldc, int64_t i0) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = i0 + blockIdx.y;
     if (t >= ccols) return;
     const int rank = max(0, min(*rank_p, (int)(npiv_cap < n ? npiv_cap : n)));
-    uint32_t v = 0u;
+    T v = 0;
     if (t < rank) {
         const int c = piv[t];
         if (c >= 0 && c < n) v = A[i * lda + c];
@@ -336,13 +338,15 @@ linac_status linac_matmul(const uint32_t* d_A, int64_t m, int64_t K, int64_t ldA
     return launch_matmul(d_A, m, K, ldA, d_B, n, ldB, make_field(p), d_C, ldC, stream);
 }
 
-linac_status linac_null_space(const uint32_t* d_R, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
-                              const int32_t* d_pivots, uint32_t p, uint32_t* d_K, int64_t kcols, int64_t ldK,
-                              int32_t* d_free, int32_t* d_nullity, cudaStream_t stream) {
-    if (m < 0 || n < 0 || ld < n || kcols < 0 || ldK < kcols || n > INT32_MAX) return LINAC_ERR_ARG;
-    if (!d_rank || !d_nullity || (n > 0 && !d_free) || (n > 0 && kcols > 0 && !d_K)) return LINAC_ERR_ARG;
-    if (m > 0 && n > 0 && (!d_R || !d_pivots)) return LINAC_ERR_ARG;
-    if (!prime_ok(p)) return LINAC_ERR_PRIME;
+}  // extern "C"
+
+namespace {
+
+// Shared by the uint32 and uint64 entry points (the prime is checked there).
+template <typename T>
+linac_status null_space_impl(const T* d_R, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
+                             const int32_t* d_pivots, T p, T* d_K, int64_t kcols, int64_t ldK, int32_t* d_free,
+                             int32_t* d_nullity, cudaStream_t stream) {
     int* status = nullptr;
     linac_status s = (linac_status)reset_status_word(stream, &status);
     if (s != LINAC_OK) return s;
@@ -362,27 +366,80 @@ linac_status linac_null_space(const uint32_t* d_R, int64_t m, int64_t n, int64_t
         for (int64_t i0 = 0; kcols > 0 && i0 < n; i0 += 65535) {
             const int64_t rows = std::min<int64_t>(65535, n - i0);
             dim3 grid((unsigned)((kcols + 255) / 256), (unsigned)rows);
-            null_space_kernel<<<grid, 256, 0, stream>>>(d_R, ld, n, pos, d_free, d_nullity, p, d_K, kcols, ldK, i0);
+            null_space_kernel<T><<<grid, 256, 0, stream>>>(d_R, ld, n, pos, d_free, d_nullity, p, d_K, kcols, ldK, i0);
             LINAC_CUDA_TRY(cudaGetLastError());
         }
     }
     return LINAC_OK;
 }
 
-linac_status linac_rank_factor(const uint32_t* d_A, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
-                               const int32_t* d_pivots, uint32_t* d_C, int64_t ccols, int64_t ldC,
-                               cudaStream_t stream) {
-    if (m < 0 || n < 0 || ld < n || ccols < 0 || ldC < ccols) return LINAC_ERR_ARG;
-    if (!d_rank || (m > 0 && ccols > 0 && (!d_C || !d_pivots || (n > 0 && !d_A)))) return LINAC_ERR_ARG;
+template <typename T>
+linac_status rank_factor_impl(const T* d_A, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
+                              const int32_t* d_pivots, T* d_C, int64_t ccols, int64_t ldC, cudaStream_t stream) {
     if (m == 0 || ccols == 0) return LINAC_OK;
     ProfScope ps(stream, PROF_DERIVED);
     for (int64_t i0 = 0; i0 < m; i0 += 65535) {   // one launch per 65535 rows (the grid's y limit)
         const int64_t rows = std::min<int64_t>(65535, m - i0);
         dim3 grid((unsigned)((ccols + 255) / 256), (unsigned)rows);
-        rank_factor_kernel<<<grid, 256, 0, stream>>>(d_A, ld, n, d_rank, d_pivots, std::min(m, n), d_C, ccols, ldC, i0);
+        rank_factor_kernel<T><<<grid, 256, 0, stream>>>(d_A, ld, n, d_rank, d_pivots, std::min(m, n), d_C, ccols, ldC,
+                                                        i0);
         LINAC_CUDA_TRY(cudaGetLastError());
     }
     return LINAC_OK;
+}
+
+linac_status null_space_args(const void* d_R, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
+                             const int32_t* d_pivots, const void* d_K, int64_t kcols, int64_t ldK,
+                             const int32_t* d_free, const int32_t* d_nullity) {
+    if (m < 0 || n < 0 || ld < n || kcols < 0 || ldK < kcols || n > INT32_MAX) return LINAC_ERR_ARG;
+    if (!d_rank || !d_nullity || (n > 0 && !d_free) || (n > 0 && kcols > 0 && !d_K)) return LINAC_ERR_ARG;
+    if (m > 0 && n > 0 && (!d_R || !d_pivots)) return LINAC_ERR_ARG;
+    return LINAC_OK;
+}
+
+linac_status rank_factor_args(const void* d_A, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
+                              const int32_t* d_pivots, const void* d_C, int64_t ccols, int64_t ldC) {
+    if (m < 0 || n < 0 || ld < n || ccols < 0 || ldC < ccols) return LINAC_ERR_ARG;
+    if (!d_rank || (m > 0 && ccols > 0 && (!d_C || !d_pivots || (n > 0 && !d_A)))) return LINAC_ERR_ARG;
+    return LINAC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+linac_status linac_null_space(const uint32_t* d_R, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
+                              const int32_t* d_pivots, uint32_t p, uint32_t* d_K, int64_t kcols, int64_t ldK,
+                              int32_t* d_free, int32_t* d_nullity, cudaStream_t stream) {
+    linac_status s = null_space_args(d_R, m, n, ld, d_rank, d_pivots, d_K, kcols, ldK, d_free, d_nullity);
+    if (s != LINAC_OK) return s;
+    if (!prime_ok(p)) return LINAC_ERR_PRIME;
+    return null_space_impl<uint32_t>(d_R, m, n, ld, d_rank, d_pivots, p, d_K, kcols, ldK, d_free, d_nullity, stream);
+}
+
+linac_status linac_null_space64(const uint64_t* d_R, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
+                                const int32_t* d_pivots, uint64_t p, uint64_t* d_K, int64_t kcols, int64_t ldK,
+                                int32_t* d_free, int32_t* d_nullity, cudaStream_t stream) {
+    linac_status s = null_space_args(d_R, m, n, ld, d_rank, d_pivots, d_K, kcols, ldK, d_free, d_nullity);
+    if (s != LINAC_OK) return s;
+    if (!prime64_ok(p)) return LINAC_ERR_PRIME;
+    return null_space_impl<uint64_t>(d_R, m, n, ld, d_rank, d_pivots, p, d_K, kcols, ldK, d_free, d_nullity, stream);
+}
+
+linac_status linac_rank_factor(const uint32_t* d_A, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
+                               const int32_t* d_pivots, uint32_t* d_C, int64_t ccols, int64_t ldC,
+                               cudaStream_t stream) {
+    linac_status s = rank_factor_args(d_A, m, n, ld, d_rank, d_pivots, d_C, ccols, ldC);
+    if (s != LINAC_OK) return s;
+    return rank_factor_impl<uint32_t>(d_A, m, n, ld, d_rank, d_pivots, d_C, ccols, ldC, stream);
+}
+
+linac_status linac_rank_factor64(const uint64_t* d_A, int64_t m, int64_t n, int64_t ld, const int32_t* d_rank,
+                                 const int32_t* d_pivots, uint64_t* d_C, int64_t ccols, int64_t ldC,
+                                 cudaStream_t stream) {
+    linac_status s = rank_factor_args(d_A, m, n, ld, d_rank, d_pivots, d_C, ccols, ldC);
+    if (s != LINAC_OK) return s;
+    return rank_factor_impl<uint64_t>(d_A, m, n, ld, d_rank, d_pivots, d_C, ccols, ldC, stream);
 }
 
 }  // extern "C"

@@ -31,8 +31,9 @@ inline bool prime_ok(uint32_t p) { return p >= 3 && p < (1u << 31) && is_prime_u
 // (device, stream); growing synchronises the stream first.
 linac_status scratch_get(cudaStream_t stream, size_t bytes, void** ptr);
 // Same, for an independent buffer `slot` (0 = dense elimination, 1 = solve's
-// augmented matrix, 2 = batched driver, 3 = limb planes, 4 = uint64
-// elimination, 5 = the uint64 solve's augmented matrix).
+// augmented matrix, 2 = batched driver, 3 = limb planes, 4 = null-space
+// column positions, 6 = uint64 elimination, 7 = the uint64 solve's
+// augmented matrix).
 linac_status scratch_get_slot(cudaStream_t stream, int slot, size_t bytes, void** ptr);
 
 // Device status word of the most recent call on this (device, stream): lives

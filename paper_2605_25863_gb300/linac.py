@@ -101,12 +101,15 @@ def lib():
         L.linac_rref64.argtypes = [vp, i64, i64, i64, u64, vp, vp, vp]
         L.linac_rref64_ex.argtypes = [vp, i64, i64, i64, u64, i64, vp, vp, ctypes.POINTER(Options), vp]
         L.linac_solve64.argtypes = [vp, i64, i64, i64, vp, i64, i64, u64, vp, i64, vp, vp, vp, vp]
+        L.linac_null_space64.argtypes = [vp, i64, i64, i64, vp, vp, u64, vp, i64, i64, vp, vp, vp]
+        L.linac_rank_factor64.argtypes = [vp, i64, i64, i64, vp, vp, vp, i64, i64, vp]
         L.linac_workspace64_bytes.argtypes = [i64, i64]
         L.linac_workspace64_bytes.restype = ctypes.c_size_t
         for name in ("linac_rref", "linac_rref_ex", "linac_solve", "linac_solve_ex",
                      "linac_rref_batched", "linac_last_device_status", "linac_version",
                      "linac_load_matrix", "linac_matmul", "linac_null_space", "linac_rank_factor",
-                     "linac_rref64", "linac_rref64_ex", "linac_solve64"):
+                     "linac_rref64", "linac_rref64_ex", "linac_solve64", "linac_null_space64",
+                     "linac_rank_factor64"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -432,3 +435,30 @@ def linac_solve64(A: torch.Tensor, B: torch.Tensor, p: int, *, stream=None):
     _check(lib().linac_solve64(pa, m, nA, ldA, pb, k, ldB, int(p), X.data_ptr(), X.stride(0), cons.data_ptr(),
                                rank.data_ptr(), piv.data_ptr(), _stream_ptr(stream)), "linac_solve64")
     return X[:nA, :k], cons[:k].bool(), rank, piv[:min(m, nA)]
+
+
+def linac_null_space64(R: torch.Tensor, rank: torch.Tensor, pivots: torch.Tensor, p: int, *,
+                       kcols: int | None = None, stream=None):
+    """linac_null_space for uint64 residues (section 5.1).  Returns (K, free,
+    nullity) with K an n x kcols int64 view."""
+    pr, m, n, ld = _matrix64(R, "R")
+    kc = n if kcols is None else int(kcols)
+    K = padded64(max(n, 1), max(kc, 1), R.device)[:n, :kc]
+    free = torch.full((max(n, 1),), -1, dtype=torch.int32, device=R.device)
+    nullity = torch.zeros(1, dtype=torch.int32, device=R.device)
+    ldk = max(K.stride(0), kc) if n else max(kc, 1)
+    _check(lib().linac_null_space64(pr, m, n, ld, rank.data_ptr(), pivots.data_ptr(), int(p),
+                                    K.data_ptr() if n else None, kc, ldk, free.data_ptr(), nullity.data_ptr(),
+                                    _stream_ptr(stream)), "linac_null_space64")
+    return K, free[:n], nullity
+
+
+def linac_rank_factor64(A: torch.Tensor, rank: torch.Tensor, pivots: torch.Tensor, *, ccols: int | None = None,
+                        stream=None) -> torch.Tensor:
+    """linac_rank_factor for uint64 residues: C = A[:, J] (section 5.1)."""
+    pa, m, n, ld = _matrix64(A, "A")
+    cc = min(m, n) if ccols is None else int(ccols)
+    C = padded64(max(m, 1), max(cc, 1), A.device)[:m, :cc]
+    _check(lib().linac_rank_factor64(pa, m, n, ld, rank.data_ptr(), pivots.data_ptr(), C.data_ptr(), cc,
+                                     max(C.stride(0), cc), _stream_ptr(stream)), "linac_rank_factor64")
+    return C

@@ -127,3 +127,13 @@ def test_uint64_entry_points_check_shapes_alignment_and_options(lib):
     assert lib.linac_solve64(fake, 4, 4, 5, fake, 2, 2, P, fake, 2, cons, ctypes.byref(rank), piv, None) == 3
     assert lib.linac_workspace64_bytes(-1, 4) == 0
     assert lib.linac_workspace64_bytes(100, 200) >= 32 * (3 * 128 + 256) * 8
+
+
+def test_uint64_derived_entry_points_check_arguments(lib):
+    fake = ctypes.c_void_p(0x1000)
+    P = 2**64 - 59
+    assert lib.linac_null_space64(fake, 3, 4, 4, fake, fake, P, fake, 4, 2, fake, fake, None) == 1   # ldK < kcols
+    assert lib.linac_null_space64(fake, 3, 4, 4, fake, fake, P, fake, 4, 4, None, fake, None) == 1
+    assert lib.linac_null_space64(fake, 3, 4, 4, fake, fake, 2**64 - 1, fake, 4, 4, fake, fake, None) == 2
+    assert lib.linac_rank_factor64(fake, 3, 4, 3, fake, fake, fake, 3, 4, None) == 1             # ld < n
+    assert lib.linac_rank_factor64(fake, 3, 4, 4, fake, fake, fake, 3, 2, None) == 1             # ldC < ccols

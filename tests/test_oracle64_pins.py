@@ -12,7 +12,9 @@ no 64-bit wrap-around) and never by the oracle itself:
 * solve: A X = B exactly for consistent right-hand sides, a right-hand side
   built outside the column space is flagged inconsistent, free variables
   are zero (section 5.2);
-* special matrices: zero, identity, p - 1 everywhere, one row, one column.
+* special matrices: zero, identity, p - 1 everywhere, one row, one column;
+* null space and rank factorisation (section 5.1): A K = 0 with the free rows
+  of K equal to -I, and A = C R.
 The primes span the range: tiny (3, 5), below 2^31, just above 2^32, the
 Mersenne prime 2^61 - 1, the largest primes below 2^63 and 2^64.
 """
@@ -193,3 +195,24 @@ def test_square_full_rank_solve_reproduces_solution(p):
     assert rank == n and cons[0]
     assert np.array_equal(X, x)
     assert np.array_equal(M[:, :n], np.eye(n, dtype=np.uint64))
+
+
+@pytest.mark.parametrize("p", [5, 2**32 + 15, 2**64 - 59])
+@pytest.mark.parametrize("mnr", [(9, 14, 5), (14, 9, 9), (10, 10, 0), (12, 12, 12)])
+def test_null_space_and_rank_factor(mnr, p):
+    """Section 5.1 in exact integers: A K = 0, the free rows of K are -I, and
+    A = C R with C = A[:, J] and R the RREF's first rank rows."""
+    m, n, r = mnr
+    g = np.random.default_rng(m * 7 + n + r)
+    Rr, piv = random_rref64(g, m, n, r, p)
+    A = matmul_exact(random_invertible64(g, m, p), Rr, p)
+    R, rank, pivots = oracle.rref64(A, p)
+    K = oracle.null_space64(R, pivots, p)
+    assert K.shape == (n, n - rank)
+    if n - rank:
+        assert not matmul_exact(A, K, p).any()
+        free = [c for c in range(n) if c not in set(pivots)]
+        assert np.array_equal(K[free], np.eye(n - rank, dtype=np.uint64) * np.uint64(p - 1))
+    C = oracle.rank_factor64(A, pivots)
+    if rank:
+        assert np.array_equal(matmul_exact(C, R[:rank], p), A)

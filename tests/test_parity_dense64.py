@@ -13,7 +13,9 @@ against the CPU oracle, bit for bit:
 * 1024 x 1056 against the oracle, and at 4096 x 4097 the identity block and
   A x = b on sampled rows checked with Python integers;
 * the range validation option, and a capture into a CUDA graph (the panel
-  kernels run on a second stream forked from the caller's).
+  kernels run on a second stream forked from the caller's);
+* null space and rank factorisation of uint64 RREFs (section 5.1) against the
+  oracle's.
 """
 import os
 
@@ -173,3 +175,31 @@ def test_rref64_captured_in_a_cuda_graph():
         assert int(rank.item()) == r0
         assert np.array_equal(piv.cpu().numpy()[:r0], piv0)
         assert np.array_equal(linac.host64(A), R0)
+
+
+@pytest.mark.parametrize("p", [5, 2**32 + 15, 2**64 - 59])
+@pytest.mark.parametrize("mnd", [(40, 60, 15), (60, 40, 0), (50, 50, 50), (130, 300, 70), (1, 1, 0)])
+def test_null_space64_and_rank_factor64_vs_oracle(mnd, p):
+    m, n, d = mnd
+    if d >= m:
+        M = np.zeros((m, n), dtype=np.uint64)
+    else:
+        M, _ = synth.rank_deficient64(m, n, d, p, seed=m + n + d)
+    A0 = linac.to_device64(M)
+    R = A0.clone()
+    rank, piv = linac.linac_rref64(R, p)
+    K, free, nullity = linac.linac_null_space64(R, rank, piv, p)
+    C = linac.linac_rank_factor64(A0, rank, piv)
+    torch.cuda.synchronize()
+    assert linac.linac_last_device_status() == 0
+    R0, r0, piv0 = oracle.rref64(M, p, nthreads=NTH)
+    assert int(rank.item()) == r0 and int(nullity.item()) == n - r0
+    Kh = linac.host64(K)
+    assert np.array_equal(Kh[:, :n - r0], oracle.null_space64(R0, piv0, p))
+    assert not Kh[:, n - r0:].any()
+    fr = free.cpu().numpy()
+    assert np.array_equal(fr[:n - r0], np.setdiff1d(np.arange(n), piv0))
+    assert (fr[n - r0:] == -1).all()
+    Ch = linac.host64(C)
+    assert np.array_equal(Ch[:, :r0], oracle.rank_factor64(M, piv0))
+    assert not Ch[:, r0:].any()
