@@ -6,12 +6,13 @@
 // columns.  Per panel:
 //   1. panel64_kernel (one block): fraction-free Gauss-Jordan of the panel
 //      columns on a window of the first NB64 + 16 remaining rows, in
-//      Montgomery form, tracking each row's combination of original rows.  If every panel column finds a pivot in the window, or
-//      the window holds every remaining row, its pivots are the panel's.
-//      Otherwise a full-height search over all remaining rows picks the pivot
-//      rows and the window elimination is repeated on exactly those rows.
-//      Output: k pivots (columns J, rows P) and E = G^(-1) for the k x k
-//      block G = A[P, J], scaled by 2^128 for the update's reduction.
+//      Montgomery form, tracking each row's combination of original rows.
+//      If every panel column finds a pivot in the window, or the window
+//      holds every remaining row, its pivots are the panel's.  Otherwise a
+//      full-height search over all remaining rows picks the pivot rows and
+//      the window elimination is repeated on exactly those rows.  Output:
+//      k pivots (columns J, rows P) and E = G^(-1) for the k x k block
+//      G = A[P, J], scaled by 2^128 for the update's reduction.
 //   2. gather64_kernel: F = A[:, J] (every row), scaled by 2^128.
 //   3. gemm64_kernel<assign>: R = E A[P, c0:n] (the pivot rows in RREF).
 //   4. gemm64_kernel<update>: A[:, c0:n] -= F R for every row; the pivot
@@ -19,10 +20,11 @@
 //   5. move64_kernel: the non-pivot rows in [r, r+k) go to the pivot rows'
 //      old places at or after r+k, R goes to rows r..r+k-1.
 //   6. advance64_kernel: pivot list, r += k.
-// No block ever waits on another block; all state is device-resident, so
-// the host issues a fixed sequence of launches per panel.  Panel kernels run
-// on a second stream, each overlapping the previous panel's update (see
-// dense64_rref).
+// Steps 4 and 5 run twice: on the panel's first 64 columns (its own and the
+// next panel's), then, after step 6, on the rest.  Steps 1 and 2 of the next
+// panel run on a second stream meanwhile (see dense64_rref).  No block ever
+// waits on another block; all state is device-resident, so the host issues a
+// fixed sequence of launches per panel.
 #include <algorithm>
 #include <climits>
 #include <map>
@@ -71,7 +73,7 @@ struct Panel64Smem {
     uint64_t T[W64_ROWS][NB64];        // row combinations: T[i][t] = coefficient of pivot t's original row
     uint64_t self[W64_ROWS];           // coefficient of the row's own original row (non-pivot rows)
     uint64_t dh[W64_ROWS];             // current head of each pivot row (Montgomery)
-    uint64_t dinv[NB64];               // head^-1 * 2^128, in Montgomery form
+    uint64_t dinv[NB64];               // head^-1 * 2^128 mod p (times T R, one Montgomery product gives T head^-1 2^128)
     int32_t rowid[W64_ROWS];           // absolute row of each slot
     int32_t slot_piv[W64_ROWS];        // pivot index of the slot, -1
     int32_t pslot[NB64], pcl[NB64];    // slot and panel column of pivot t
