@@ -3,7 +3,9 @@
  *
  * The library computes the reduced row-echelon form (RREF), rank, pivot
  * columns and particular solutions of linear systems over the prime field
- * Z/pZ for odd primes p < 2^31, with entries stored as uint32_t residues.
+ * Z/pZ for odd primes p < 2^31, with entries stored as uint32_t residues,
+ * and (the *64 entry points near the end) for odd primes p < 2^64 with
+ * uint64_t residues.
  * It follows the method of "Linac: linear algebra with CUDA over finite
  * fields": partially pivoted Gauss-Jordan elimination to RREF (section 3.2,
  * "Gaussian elimination on GPUs"), the RREF kept in the input's shape with
@@ -13,13 +15,15 @@
  * Conventions shared by every entry point:
  *  - Pointers named d_* are DEVICE pointers on the current CUDA device; the
  *    caller allocates and owns them.  Matrices are row-major with a leading
- *    dimension (ld, in elements) that is a multiple of 4 and >= the number of
- *    columns, and must start 16-byte aligned (section 3.2, "Number types":
- *    rows are padded so 128-bit accesses never cross a row).
+ *    dimension (ld, in elements) that is a multiple of 4 (of 2 for uint64
+ *    residues) and >= the number of columns, and must start 16-byte aligned
+ *    (section 3.2, "Number types": rows are padded so 128-bit accesses never
+ *    cross a row).
  *  - Entries must be canonical residues in [0, p).  Larger entries are not
  *    reduced and give undefined results.
- *  - p must be an odd prime below 2^31 (checked on the host with a
- *    deterministic Miller-Rabin test); otherwise LINAC_ERR_PRIME.
+ *  - p must be an odd prime below 2^31 (below 2^64 for the *64 entry
+ *    points), checked on the host with a deterministic Miller-Rabin test;
+ *    otherwise LINAC_ERR_PRIME.
  *  - All calls are asynchronous and ordered on `stream` (0 = legacy default
  *    stream).  Argument errors are returned immediately; errors found on the
  *    device (a bounded wait that gave up) are written to the per-call device
