@@ -20,7 +20,8 @@ Also reported: the dominant kernel's roofline (CUDA events around each of
 its launches, on the launch stream), the e2e rate through the public API
 with host buffers (pinned H2D, RREF, D2H each step), the CPU oracle on a
 bounded sample of the same workload, the u8-limb tensor path beside the
-plain path, the batched workload (systems/s) and the shared-pattern batch.
+plain path, the batched workload (systems/s), the shared-pattern batch, the
+construction leg and the uint64 leg (RREF of 8192 x 8448 at p = 2^64 - 59).
 
 --impl reference times the CPU oracle alone (rank 0), on bounded samples of
 the same workload.
