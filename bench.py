@@ -47,8 +47,6 @@ if ROOT not in sys.path:
 METRIC = "mod-p MACs/s for RREF at n=32768 (tensor vs plain path); batched systems/s"
 UNIT = "field MAC/s"
 P31 = 2**31 - 1
-SMS = 152                 # GB300 SM count
-SM_MAX_MHZ = 2070.0       # GB300 maximum SM clock
 # 64-bit-accumulating integer multiply-adds (mad.wide.s32) per SM per clock:
 # 4 schedulers x a 16-lane multiply pipe, two passes per wide multiply-add
 # (ncu: ~4 pipe cycles per 32-thread warp instruction on GB300)
@@ -118,6 +116,26 @@ def replica_rate(local_ms: float, local_work: float, world: int, device) -> tupl
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         max_ms = float(t.item())
     return world * local_work / (max_ms / 1000.0), max_ms
+
+
+def device_sms_and_max_clock(dev) -> tuple[int, float, str]:
+    """SM count (CUDA device properties) and maximum SM clock in MHz
+    (nvidia-smi clocks.max.sm) of the benchmarked device."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    sms = int(props.multi_processor_count)
+    uuid = getattr(props, "uuid", None)
+    cmd = ["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"]
+    if uuid:
+        cmd.insert(1, f"--id=GPU-{uuid}")
+    try:
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=30).stdout.strip().splitlines()
+        return sms, float(out[0]), "nvidia-smi clocks.max.sm"
+    except Exception as e:   # no nvidia-smi: the clock rate CUDA reports
+        clk = getattr(props, "clock_rate", 0) / 1000.0
+        if clk <= 0:
+            raise RuntimeError(f"cannot read the maximum SM clock: {e}")
+        return sms, clk, "CUDA device clock rate"
 
 
 def update_src_sha() -> str:
@@ -361,7 +379,8 @@ def run_ours(args):
     traffic = None
     if upd_name == "update_plain" and upd_launches and update_src_sha() == UPDATE_SRC_SHA:
         traffic = UPDATE_BYTES_PER_OUTPUT * update_outputs(m, n, nb) * args.steps / upd_launches
-    peak = SMS * IMAD_WIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / imad_per_mac
+    sms, sm_max_mhz, clk_src = device_sms_and_max_clock(dev)
+    peak = sms * IMAD_WIDE_PER_SM_CLK * sm_max_mhz * 1e6 / imad_per_mac
     kernel_times = {k: {"launches": v[0], "total_ms": round(v[1], 3),
                         "share": round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4)}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -379,7 +398,8 @@ def run_ours(args):
                      "traffic": traffic,
                      "traffic_basis": "ncu DRAM bytes per output of the 8192 x 8448 capture x outputs per launch"
                                       if traffic is not None else "kernel changed since the ncu capture",
-                     "peak_basis": f"{SMS} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x {SM_MAX_MHZ:.0f} MHz"
+                     "peak_basis": f"{sms} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x {sm_max_mhz:.0f} MHz"
+                                   f" ({clk_src})"
                                    f" / {imad_per_mac:.3f} per field MAC"
                                    f" ({'folds on the ALU pipe' if shift_fold else f'fold every {fold} on the multiply pipe'})",
                      "avg_launch_ms": upd_ms / max(1, upd_launches), "launches": upd_launches},
@@ -717,8 +737,8 @@ def main():
         import torch
         import __graft_entry__
         __graft_entry__.build()
-        from paper_2605_25863_gb300 import linac
-        r = linac.linac_measure_int_rates()
+        from paper_2605_25863_gb300 import probes
+        r = probes.measure_int_rates()
         r["imad_per_sm_per_clk"] = r["imad_wide_per_s"] / (r["sm_count"] * r["sm_clock_khz"] * 1e3)
         r["device"] = torch.cuda.get_device_name(0)
         print(json.dumps(r))

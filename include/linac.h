@@ -63,7 +63,10 @@ typedef enum {
 typedef enum {
     LINAC_PATH_AUTO = 0,   /* fastest measured path on this device */
     LINAC_PATH_PLAIN = 1,  /* CUDA cores: lazy signed 64-bit accumulation */
-    LINAC_PATH_LIMB = 2    /* integer tensor pipe: four u8 limbs per residue */
+    LINAC_PATH_LIMB = 2,   /* integer tensor pipe: four u8 limbs per residue */
+    LINAC_PATH_CRT = 3     /* integer tensor pipe: residues modulo nine small
+                              moduli (s8), exact Chinese-remainder
+                              reconstruction of each output */
 } linac_path;
 
 typedef struct {
@@ -109,7 +112,10 @@ linac_status linac_rref(uint32_t *d_A, int64_t m, int64_t n, int64_t ld, uint32_
  *     it before any stream capture on that device;
  *   - all calls share the array: calls that overlap on the GPU race and must
  *     be serialised by the caller;
- *   - device-side wait failures are not reported by linac_last_device_status.
+ *   - a device-side failure (a bounded wait that gave up, see
+ *     linac_set_wait_limit) is not reported by linac_last_device_status:
+ *     *d_rank is then set to minus the status (-6 for LINAC_ERR_TIMEOUT),
+ *     and the matrix and pivots are undefined.
  */
 linac_status linac_rref_noalloc(uint32_t *d_A, int64_t m, int64_t n, int64_t ld, uint32_t p,
                                 int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
@@ -371,26 +377,30 @@ void linac_profile_reset(void);
 int linac_profile_read(linac_profile_entry *out, int max_entries);
 long long linac_launch_count(void);
 
-/* Throughput of the integer pipes the two trailing-update paths run on,
- * measured by short saturating probes on the current device (allocates a
- * small buffer; synchronises `stream`): thread-level mad.wide.s32 per second
- * (plain path), u8 multiply-adds per second of mma.sync m16n8k32 (limb path)
- * and of dp4a.  Diagnostic only; the paper has no counterpart. */
-typedef struct {
-    double imad_wide_per_s;
-    double imma_u8_mac_per_s;
-    double dp4a_u8_mac_per_s;
-    double sm_clock_khz;      /* nominal maximum SM clock */
-    int sm_count;
-    /* one block of 512 threads per SM: warps 0-7 run mad.wide.s32, warps 8-15
-     * mma.sync u8; time with only the first group working, only the second,
-     * and both at once (ms) */
-    double coissue_imad_only_ms;
-    double coissue_imma_only_ms;
-    double coissue_both_ms;
-} linac_int_rates;
+/*
+ * Failure detection.  Every wait of one thread block on others (the arrival
+ * barrier of the dense elimination's full-height pivot search, section 3.2
+ * "Pivoting") is bounded: after the limit it records LINAC_ERR_TIMEOUT in the
+ * device status word (linac_last_device_status; for linac_rref_noalloc, a
+ * negative rank) and every block returns, so a fault elsewhere never hangs
+ * the device.  The results of a call that timed out are not defined; the
+ * next call starts afresh.
+ *
+ * linac_set_wait_limit -- limit of those waits in SM clock cycles for every
+ * later launch from this process (0 restores the default of 4e9 cycles,
+ * about 2 s).  Errors: LINAC_ERR_ARG for a negative value.
+ */
+linac_status linac_set_wait_limit(int64_t cycles);
 
-linac_status linac_measure_int_rates(linac_int_rates *out, cudaStream_t stream);
+/*
+ * linac_debug_inject_wait_failure -- test support (the paper has no
+ * counterpart).  While on, the arrival barrier of the full-height pivot
+ * search waits for one more arrival than its blocks make: nothing ever
+ * completes it, so every block's wait runs out after the wait limit and the
+ * call reports LINAC_ERR_TIMEOUT.  It lets tests check the timeout path
+ * without faulting or hanging the GPU.  Off by default; 0 turns it off.
+ */
+void linac_debug_inject_wait_failure(int32_t on);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t linac_version(void);

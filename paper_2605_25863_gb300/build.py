@@ -1,8 +1,9 @@
 """Build the sm_103a shared library liblinac.so in-tree with nvcc.
 
 Each .cu translation unit under csrc/ is compiled in parallel into _build/,
-then linked into _lib/liblinac.so (static CUDA runtime).  The build is
-skipped when the library is newer than every source and header.
+then linked into _lib/liblinac.so (static CUDA runtime).  The benchmark's
+pipe-rate probes (probes/) are linked into a separate _lib/liblinac_probes.so.
+Each build is skipped when its library is newer than every source and header.
 """
 from __future__ import annotations
 
@@ -17,18 +18,20 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblinac.so")
+PROBES = os.path.join(HERE, "probes")
+PROBES_LIB = os.path.join(LIBDIR, "liblinac_probes.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", INCLUDE, "-I", CSRC]
 
 
-def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+def sources(d=CSRC):
+    return sorted(os.path.join(d, f) for f in os.listdir(d) if f.endswith(".cu"))
 
 
-def _inputs():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+def _inputs(d=CSRC):
+    files = [os.path.join(d, f) for f in os.listdir(d) if not f.startswith("__")]
     files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     files.append(os.path.abspath(__file__))
     return files
@@ -41,23 +44,30 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblinac.so")
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB, d=CSRC) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _inputs())
+    t = os.path.getmtime(lib)
+    return all(os.path.getmtime(f) <= t for f in _inputs(d))
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    if not force and up_to_date():
-        return LIB
+    """Builds liblinac.so and liblinac_probes.so; returns liblinac.so's path."""
+    _build_one(LIB, CSRC, "", force, verbose, extra_flags)
+    _build_one(PROBES_LIB, PROBES, "probe_", force, verbose, extra_flags)
+    return LIB
+
+
+def _build_one(lib, srcdir, prefix, force, verbose, extra_flags):
+    if not force and up_to_date(lib, srcdir):
+        return lib
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     cc = nvcc()
     flags = FLAGS + list(extra_flags or [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(BUILD, prefix + os.path.basename(src).replace(".cu", ".o"))
         cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -67,14 +77,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
-        objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(compile_one, sources(srcdir)))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points declared in include/linac.h: argument
 // checks, the prime test, per-prime constants, scratch memory, dispatch.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -152,19 +153,47 @@ std::mutex g_mu;
 std::map<std::tuple<int, cudaStream_t, int>, ScratchBuf> g_scratch;
 std::map<std::pair<int, cudaStream_t>, int*> g_status;
 int g_sm_count[64] = {0};
+int g_smem_optin[64] = {0};
 }  // namespace
 
-int sm_count() {
+// Attribute of the CURRENT device, cached per device for the first 64
+// device ordinals (queried every time beyond them).
+static int device_attr(cudaDeviceAttr attr, int* cache) {
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return 148;
-    if (!g_sm_count[dev]) {
-        int v = 0;
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        g_sm_count[dev] = v > 0 ? v : 1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
     }
-    return g_sm_count[dev];
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, attr, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    if (dev >= 0 && dev < 64) cache[dev] = v;
+    return v;
 }
+
+int sm_count() {
+    const int v = device_attr(cudaDevAttrMultiProcessorCount, g_sm_count);
+    return v > 0 ? v : 1;
+}
+
+namespace {
+std::atomic<long long> g_wait_cycles{0};
+std::atomic<unsigned> g_wait_extra{0};
+}  // namespace
+
+WaitLimit wait_limit() {
+    WaitLimit w;
+    const long long c = g_wait_cycles.load();
+    w.spin_cycles = c > 0 ? c : kSpinCycles;
+    w.extra_arrivals = g_wait_extra.load();
+    w.pad = 0;
+    return w;
+}
+
+int max_smem_optin() { return device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, g_smem_optin); }
 
 linac_status scratch_get_slot(cudaStream_t stream, int slot, size_t bytes, void** ptr) {
     int dev = 0;
@@ -236,7 +265,7 @@ linac_status check_matrix64(const void* d, int64_t m, int64_t n, int64_t ld) {
 
 linac_status check_opts(const linac_options* o) {
     if (!o) return LINAC_OK;
-    if (o->path < LINAC_PATH_AUTO || o->path > LINAC_PATH_LIMB) return LINAC_ERR_ARG;
+    if (o->path < LINAC_PATH_AUTO || o->path > LINAC_PATH_CRT) return LINAC_ERR_ARG;
     if (o->nb < 0 || o->nb > NB_MAX || (o->nb % UPD_BK) != 0) return LINAC_ERR_ARG;
     return LINAC_OK;
 }
@@ -432,6 +461,14 @@ const char* linac_status_string(linac_status s) {
     return "unknown status";
 }
 
-int32_t linac_version(void) { return 100; }
+linac_status linac_set_wait_limit(int64_t cycles) {
+    if (cycles < 0) return LINAC_ERR_ARG;
+    g_wait_cycles.store(cycles);
+    return LINAC_OK;
+}
+
+void linac_debug_inject_wait_failure(int32_t on) { g_wait_extra.store(on ? 1u : 0u); }
+
+int32_t linac_version(void) { return 200; }
 
 }  // extern "C"

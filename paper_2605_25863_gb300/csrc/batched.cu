@@ -910,7 +910,8 @@ static int bt_group_occupancy(int blo, int bhi, const BtWidths& wd, int sh, size
         smem = std::max(smem, bt_layout(bt_bucket_max(b), wd.nb[b]).total);
     }
     int max_smem = 0;
-    if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess) return 0;
+    max_smem = max_smem_optin();
+    if (max_smem <= 0) return 0;
     if (smem + sizeof(BtSmall<64>) > (size_t)max_smem) return 0;
     const void* fn = bt_kernel_fn(wd.nb[blo], sh);
     if (!fn) return 0;
@@ -1077,7 +1078,8 @@ __global__ void tune_fill_kernel(uint32_t* data, int64_t words, uint32_t p, uint
 
 linac_status batched_tune(const Field& f, int32_t* nb_out, cudaStream_t stream) {
     int max_smem = 0;
-    LINAC_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
+    max_smem = max_smem_optin();
+    if (max_smem <= 0) return LINAC_ERR_CUDA;
     const int cands[3] = {16, 32, 64};
     for (int b = 0; b < BT_NBUCKETS; ++b) {
         const int hi = bt_bucket_max(b), lo = b ? bt_bucket_max(b - 1) + 1 : 8;
@@ -1175,7 +1177,8 @@ linac_status batched_tune(const Field& f, int32_t* nb_out, cudaStream_t stream) 
 
 linac_status batched_set_nb(const int32_t* nb) {
     int max_smem = 0;
-    LINAC_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
+    max_smem = max_smem_optin();
+    if (max_smem <= 0) return LINAC_ERR_CUDA;
     for (int b = 0; b < BT_NBUCKETS; ++b) {
         const int v = nb[b];
         if (v != 0 && v != 16 && v != 32 && v != 64) return LINAC_ERR_ARG;

@@ -232,7 +232,7 @@ window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int
 
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, int S_max,
-             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status) {
+             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status, WaitLimit wl) {
     extern __shared__ __align__(16) uint32_t sm[];
     const int SW = w + 1;
     uint32_t* P = sm;
@@ -279,7 +279,7 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
         __syncwarp();
         if (lane == 0) {
             unsigned int* counter = &st->bar.count;
-            const unsigned int target = (unsigned)(c0 + col + 1) * (unsigned)G;
+            const unsigned int target = (unsigned)(c0 + col + 1) * (unsigned)G + wl.extra_arrivals;
             asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
             const long long t0 = clock64();
             for (unsigned int it = 0;; ++it) {
@@ -288,7 +288,7 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
                 if ((int)(v - target) >= 0) break;
                 if ((it & 255u) == 255u) {
                     if (*(volatile int*)status != 0) { s_ok = 0; break; }
-                    if (clock64() - t0 > kSpinCycles) {
+                    if (clock64() - t0 > wl.spin_cycles) {
                         atomicCAS(status, 0, (int)LINAC_ERR_TIMEOUT);
                         s_ok = 0;
                         break;
@@ -679,7 +679,8 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
     const int S_max = (int)((m + G - 1) / G);
     size_t psmem = panel_smem(S_max, nb);
     int max_smem = 0;
-    LINAC_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
+    max_smem = max_smem_optin();
+    if (max_smem <= 0) return LINAC_ERR_CUDA;
     while (psmem > (size_t)max_smem - 1024 && nb > UPD_BK) {   // very tall matrices: narrower panels
         nb -= UPD_BK;
         psmem = panel_smem(S_max, nb);
@@ -721,6 +722,15 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
         limb.Rl = (uint8_t*)lb + fbytes;
         limb_ok = true;
     }
+    CrtScratch crt{};
+    bool crt_ok = false;
+    if (path == LINAC_PATH_CRT) {
+        void* cb = nullptr;
+        st_ = scratch_get_slot(stream, 8, crt_scratch_bytes(m, n), &cb);
+        if (st_ != LINAC_OK) return st_;
+        crt_scratch_layout(cb, m, n, &crt);
+        crt_ok = true;
+    }
     {
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((npiv + 255) / 256, 1024));
         ProfScope ps(stream, PROF_INIT);
@@ -741,7 +751,8 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
             int64_t m_ = m, ld_ = ld;
             int c0_ = (int)c0, w_ = w, S_ = S_max;
             Field f_ = f;
-            void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status};
+            WaitLimit wl = wait_limit();
+            void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status, &wl};
             ProfScope ps(stream, PROF_PANEL);
             LINAC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_kernel, dim3(G), dim3(PANEL_THREADS),
                                                        args, psmem, stream));
@@ -773,7 +784,7 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
             move_kernel<<<NB_MAX, 256, 0, stream>>>(dA, ld, n, (int)c0, st, Ft, L.ldF);
         }
         linac_status us = launch_update(path, dA, m, n, ld, (int)c0, f, st, Ft, L.ldF, R, L.ldW,
-                                       limb_ok ? &limb : nullptr, stream);
+                                       limb_ok ? &limb : nullptr, crt_ok ? &crt : nullptr, status, stream);
         if (us != LINAC_OK) return us;
         {
             ProfScope ps(stream, PROF_FINISH);

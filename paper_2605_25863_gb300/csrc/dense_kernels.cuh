@@ -22,7 +22,7 @@ window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int
               uint32_t* __restrict__ panelU, int G);
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, int S_max,
-             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status);
+             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status, WaitLimit wl);
 __global__ void __launch_bounds__(256)
 gather_f_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f,
                 const DenseState* __restrict__ st, int32_t* __restrict__ Ft, int64_t ldF);

@@ -240,6 +240,19 @@ __device__ __forceinline__ uint32_t inverse_fermat(uint32_t a, const Field& f) {
 // the kernel return, so a fault elsewhere can never hang the device.
 constexpr long long kSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
 
+// Limit of the panel kernel's arrival wait, passed by value at every launch:
+// spin_cycles clocks (kSpinCycles unless the caller set another limit with
+// linac_set_wait_limit), and extra_arrivals added to the arrival target.
+// extra_arrivals is 0 except when a test injects a wait failure
+// (linac_debug_inject_wait_failure): the target then exceeds the arrivals
+// the grid makes, so every block's wait runs out and returns
+// LINAC_ERR_TIMEOUT through the status word.
+struct WaitLimit {
+    long long spin_cycles;
+    unsigned int extra_arrivals;
+    unsigned int pad;
+};
+
 struct GridBarrier {
     unsigned int count;
     unsigned int gen;

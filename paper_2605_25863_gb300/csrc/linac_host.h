@@ -33,7 +33,7 @@ linac_status scratch_get(cudaStream_t stream, size_t bytes, void** ptr);
 // Same, for an independent buffer `slot` (0 = dense elimination, 1 = solve's
 // augmented matrix, 2 = batched driver, 3 = limb planes, 4 = null-space
 // column positions, 6 = uint64 elimination, 7 = the uint64 solve's
-// augmented matrix).
+// augmented matrix, 8 = residue planes of the multi-modular update).
 linac_status scratch_get_slot(cudaStream_t stream, int slot, size_t bytes, void** ptr);
 
 // Device status word of the most recent call on this (device, stream): lives
@@ -51,8 +51,16 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
         }                                                      \
     } while (0)
 
-// Number of SMs on the current device (cached).
+// Limit of the device-side waits for the next launch: the limit set with
+// linac_set_wait_limit (kSpinCycles by default) and the injected failure of
+// linac_debug_inject_wait_failure.
+WaitLimit wait_limit();
+
+// Number of SMs on the current device (cached per device).
 int sm_count();
+// Opt-in shared memory per block of the current device in bytes (cached per
+// device; 0 if the query failed).
+int max_smem_optin();
 
 // Dense elimination driver (dense.cu): in-place RREF of the m x n matrix with
 // pivots searched in [0, nsearch).  Scratch comes from scratch_get.

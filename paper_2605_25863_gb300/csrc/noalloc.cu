@@ -24,8 +24,15 @@
 //    reading it.  Calls whose executions overlap on the GPU (two streams, or
 //    two host threads) race on the array and give wrong results: serialise
 //    them.
-//  - A device-side wait that gives up (it never does in correct operation)
-//    is recorded in the array, not in linac_last_device_status().
+//  - Pivots come from the same places as in linac_rref: the window of the
+//    first nb + 16 remaining rows on an 8-block cluster, and the grid-wide
+//    search when the window lacks a pivot.
+//  - A device-side failure (a bounded wait that gave up, which never happens
+//    in correct operation, or a zero pivot head) is recorded in the array's
+//    status word, not in linac_last_device_status().  A final one-thread
+//    kernel then writes minus that status to *d_rank (-6 for
+//    LINAC_ERR_TIMEOUT), so the caller sees the failure in the output it
+//    already reads, without another call.
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -90,6 +97,12 @@ linac_status noalloc_base(void** out) {
     return LINAC_OK;
 }
 
+// A failure recorded in the status word replaces the rank by its negation.
+__global__ void noalloc_report_kernel(const int* __restrict__ status, int32_t* d_rank) {
+    const int v = *status;
+    if (v != 0) *d_rank = -v;
+}
+
 }  // namespace
 
 }  // namespace linac
@@ -141,15 +154,18 @@ extern "C" linac_status linac_rref_noalloc(uint32_t* d_A, int64_t m, int64_t n, 
     LINAC_CUDA_TRY(cudaGetLastError());
     if (m == 0 || n == 0) return LINAC_OK;
 
+    const WaitLimit wl0 = wait_limit();
     for (int64_t c0 = 0; c0 < n; c0 += nb) {
         const int w = (int)std::min<int64_t>(nb, n - c0);
         const int64_t ncols = n - c0;
+        window_kernel<<<WIN_CTAS, WIN_THREADS, 0, stream>>>(d_A, m, ld, (int)c0, w, f, st, panelU, G);
         {
             const uint32_t* Mc = d_A;
             int64_t m_ = m, ld_ = ld;
             int c0_ = (int)c0, w_ = w, S_ = S_max;
             Field f_ = f;
-            void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status};
+            WaitLimit wl = wl0;
+            void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status, &wl};
             LINAC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_kernel, dim3(G), dim3(PANEL_THREADS),
                                                        args, psmem, stream));
         }
@@ -161,10 +177,13 @@ extern "C" linac_status linac_rref_noalloc(uint32_t* d_A, int64_t m, int64_t n, 
         s = launch_gemm_assign(f, st, Et, NB_MAX, W, L.ldW, ncols, R, L.ldW, stream);
         if (s != LINAC_OK) return s;
         move_kernel<<<NB_MAX, 256, 0, stream>>>(d_A, ld, n, (int)c0, st, Ft, L.ldF);
-        s = launch_update(LINAC_PATH_PLAIN, d_A, m, n, ld, (int)c0, f, st, Ft, L.ldF, R, L.ldW, nullptr, stream);
+        s = launch_update(LINAC_PATH_PLAIN, d_A, m, n, ld, (int)c0, f, st, Ft, L.ldF, R, L.ldW, nullptr, nullptr,
+                         status, stream);
         if (s != LINAC_OK) return s;
         finish_kernel<<<1, NB_MAX, 0, stream>>>(st, d_pivots, d_rank);
         LINAC_CUDA_TRY(cudaGetLastError());
     }
+    noalloc_report_kernel<<<1, 1, 0, stream>>>(status, d_rank);
+    LINAC_CUDA_TRY(cudaGetLastError());
     return LINAC_OK;
 }

@@ -24,7 +24,8 @@ long long g_count[PROF_NCLASSES];
 const char* g_names[PROF_NCLASSES] = {"init", "panel", "gather_f", "gather_w", "inverse", "trsm", "move",
                                       "update_plain", "update_limb", "limb_split", "finish", "batched",
                                       "solve_pack", "solve_extract", "validate", "pattern", "matmul",
-                                      "load_matrix", "derived", "u64_panel", "u64_update"};
+                                      "load_matrix", "derived", "u64_panel", "u64_update",
+                                      "update_crt", "crt_split"};
 
 cudaEvent_t take_event() {
     if (!g_pool.empty()) {

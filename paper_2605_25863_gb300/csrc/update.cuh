@@ -34,13 +34,23 @@ struct LimbScratch {
     int64_t m_pad, n_pad;
 };
 
+// Extra scratch used by the multi-modular path (s8 residue planes of F and R
+// for nine moduli; update_crt.cu).
+struct CrtScratch {
+    uint8_t* Fr;      // 9 planes x m_pad rows x 128 bytes
+    uint8_t* Rr;      // 9 planes x n_pad columns x 128 bytes
+    int64_t m_pad, n_pad;
+};
+size_t crt_scratch_bytes(int64_t m, int64_t n);
+void crt_scratch_layout(void* base, int64_t m, int64_t n, CrtScratch* out);
+
 // M[d, c0:n] <- M[d, c0:n] - F[d] R (rows d outside [r, r+k)) and
 // M[r+t, c0:n] <- R[t] (t < k).  F is stored transposed (Ft: k x ldF, balanced
 // int32), R row-major (k x ldR, balanced int32, columns relative to c0).
 linac_status launch_update(int path, uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0,
                            const Field& f, const DenseState* st, const int32_t* Ft, int64_t ldF,
                            const int32_t* R, int64_t ldR, const LimbScratch* limb,
-                           cudaStream_t stream);
+                           const CrtScratch* crt, int* status, cudaStream_t stream);
 
 // R[t][j] <- balanced(sum_s E[t][s] W[s][j]) for t < kpad(k), j < ncols, with
 // Et = E transposed (kpad x ldE) and W (kpad x ldW), both balanced int32.

@@ -1,0 +1,424 @@
+// update_crt.cu -- trailing update C <- C - F R (mod p) on the integer tensor
+// pipe by multi-modular (residue number system) arithmetic.
+//
+// F (m x k) and R (k x N) hold balanced residues, |x| <= h = (p - 1)/2, so the
+// exact integer product D = F R satisfies |D| <= k h^2 < 2^67 for k <= 128
+// and p < 2^31.  Nine pairwise coprime moduli m_i <= 256 (CRT_MODULI below)
+// have product M > 2^71.4 > 2 * 2^67, so D is fixed by its residues D mod m_i
+// (Chinese remainder theorem) and recovered exactly:
+//
+//   1. Split (per panel): F_i = F mod m_i and R'_i = (R mod m_i) y_i mod m_i,
+//      both balanced, |x| <= 128, stored as s8; y_i = (M/m_i)^(-1) mod m_i.
+//   2. For each i, D'_i = F_i R'_i on mma.sync m16n8k32 s8 x s8 -> s32 (the
+//      integer MMA of sm_103a; tcgen05 kind::i8 does not exist there).
+//      Exact: |D'_i| <= k * 128^2 <= 2^21.
+//   3. t_i = D'_i mod m_i = (D mod m_i) y_i mod m_i in [0, m_i); then
+//      D = sum_i t_i (M/m_i) - alpha M with the integer alpha that puts D in
+//      (-M/2, M/2).  Because |D|/M < 2^-4.4, alpha is the nearest integer to
+//      sum_i t_i / m_i; it is found in 16-bit fixed point,
+//      S = sum_i t_i floor(2^16 / m_i): S undershoots 2^16 sum_i t_i / m_i by
+//      less than sum_i t_i < 2304, and 2^16 |D|/M < 3146, so
+//      alpha = floor((S + 2^15) / 2^16) exactly.
+//   4. D mod p = (sum_i t_i ((M/m_i) mod p) + alpha ((-M) mod p)) mod p, summed
+//      exactly in 64 bits (< 2^43) and reduced once (Barrett).
+// No floating point anywhere.
+//
+// Data: per panel the split kernels write the residue planes Fr[i][row][.]
+// (the k <= 128 residues of one row of F, 128 bytes) and Rr[i][col][.] (one
+// column of R').  Within every 128-byte row the 16-byte chunk c is stored at
+// chunk c ^ (row & 7), so a 64-row tile copied contiguously into shared
+// memory is already swizzled and the fragment loads are free of bank
+// conflicts.  Update: one 256-thread block per 64 x 64 output tile, two
+// blocks per SM; the tile's nine (A_i, B_i) pairs (8 KB + 8 KB each) stream
+// through a three-stage ring of shared-memory buffers filled by bulk
+// asynchronous copies (cp.async.bulk, the Blackwell TMA engine) that
+// complete on mbarriers.  Each of the 8 warps computes 32 x 16 outputs.
+#include <algorithm>
+
+#include "linac_host.h"
+#include "profile.h"
+#include "update.cuh"
+
+namespace linac {
+
+namespace {
+
+constexpr int CRT_L = 9;
+constexpr uint32_t CRT_MODULI[CRT_L] = {256, 255, 253, 251, 247, 241, 239, 233, 229};
+constexpr int CRT_BM = 64, CRT_BN = 64;
+constexpr int CRT_KB = NB_MAX;                      // bytes per residue row (k <= 128)
+constexpr int CRT_THREADS = 256;
+constexpr int CRT_STAGES = 3;
+constexpr int CRT_A_BYTES = CRT_BM * CRT_KB;        // 8 KB
+constexpr int CRT_B_BYTES = CRT_BN * CRT_KB;        // 8 KB
+constexpr int CRT_STAGE_BYTES = CRT_A_BYTES + CRT_B_BYTES;
+constexpr size_t CRT_SMEM = (size_t)CRT_STAGES * CRT_STAGE_BYTES + 64;
+
+}  // namespace
+
+// Per-prime constants of the reconstruction (computed on the host).
+struct CrtConsts {
+    uint32_t m[CRT_L];      // the moduli
+    uint32_t y[CRT_L];      // (M / m_i)^(-1) mod m_i
+    uint32_t off30[CRT_L];  // m_i ceil(2^30 / m_i): makes a balanced residue of p non-negative
+    uint32_t off21[CRT_L];  // m_i ceil(2^21 / m_i): makes D'_i non-negative
+    uint32_t mgf[CRT_L];    // floor(2^32 / m_i)
+    uint32_t mgc[CRT_L];    // ceil(2^32 / m_i)
+    uint32_t w16[CRT_L];    // floor(2^16 / m_i)
+    uint32_t wp[CRT_L];     // (M / m_i) mod p
+    uint32_t negMp;         // (-M) mod p
+};
+
+CrtConsts make_crt(uint32_t p) {
+    CrtConsts c{};
+    unsigned __int128 M = 1;
+    for (int i = 0; i < CRT_L; ++i) M *= CRT_MODULI[i];
+    for (int i = 0; i < CRT_L; ++i) {
+        const uint32_t mi = CRT_MODULI[i];
+        c.m[i] = mi;
+        uint64_t Mi_mod = 1, Mi_p = 1;
+        for (int j = 0; j < CRT_L; ++j)
+            if (j != i) {
+                Mi_mod = Mi_mod * CRT_MODULI[j] % mi;
+                Mi_p = Mi_p * CRT_MODULI[j] % p;
+            }
+        uint32_t y = 0;
+        for (uint32_t t = 1; t < mi; ++t)
+            if (Mi_mod * t % mi == 1) { y = t; break; }
+        c.y[i] = y;
+        c.off30[i] = (uint32_t)(((1ull << 30) + mi - 1) / mi * mi);
+        c.off21[i] = (uint32_t)(((1ull << 21) + mi - 1) / mi * mi);
+        c.mgf[i] = (uint32_t)((1ull << 32) / mi);
+        c.mgc[i] = (uint32_t)(((1ull << 32) + mi - 1) / mi);
+        c.w16[i] = (uint32_t)((1u << 16) / mi);
+        c.wp[i] = (uint32_t)Mi_p;
+    }
+    const uint64_t Mp = (uint64_t)(M % p);
+    c.negMp = (uint32_t)((p - Mp) % p);
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Residue planes
+
+// Balanced residue of a balanced x (|x| <= 2^30) modulo m (m <= 256):
+// u = x + off30 lies in [0, 2^31 + 256); the quotient estimate
+// floor(u floor(2^32/m) / 2^32) is floor(u/m) or one less, so one conditional
+// subtraction gives r = u mod m.
+__device__ __forceinline__ uint32_t small_mod30(int32_t x, uint32_t m, uint32_t off30, uint32_t mgf) {
+    const uint32_t u = (uint32_t)x + off30;   // exact: the true sum lies in [0, 2^32)
+    uint32_t r = u - __umulhi(u, mgf) * m;
+    if (r >= m) r -= m;
+    return r;
+}
+
+// u mod m for u < 2^24: floor(u ceil(2^32/m) / 2^32) = floor(u/m) exactly
+// (the rounding error u (ceil(2^32/m) m - 2^32) / (m 2^32) < u / 2^32 < 1/m).
+__device__ __forceinline__ uint32_t small_mod24(uint32_t u, uint32_t m, uint32_t mgc) {
+    return u - __umulhi(u, mgc) * m;
+}
+
+__device__ __forceinline__ int32_t small_balanced(uint32_t r, uint32_t m) {
+    return r > (m - 1) / 2 ? (int32_t)r - (int32_t)m : (int32_t)r;
+}
+
+// Planes of a k x ncols operand T stored t-major (T[t][x], leading dimension
+// ldT, balanced int32; rows t >= k read as zero): out[i][x][.] holds the 128
+// residues T[0..127][x] mod m_i (times y_i when SCALE), balanced s8, chunk c
+// of row x at chunk c ^ (x & 7).  One block per 64 values of x.
+template <bool SCALE>
+__global__ void __launch_bounds__(256)
+crt_split_kernel(const int32_t* __restrict__ T, int64_t ldT, int64_t nx, const DenseState* __restrict__ st,
+                 CrtConsts cc, uint8_t* __restrict__ out, int64_t x_pad) {
+    __shared__ int32_t tile[CRT_KB][65];
+    const int k = st->k;
+    if (k == 0) return;
+    const int64_t x0 = (int64_t)blockIdx.x * 64;
+    for (int e = threadIdx.x; e < CRT_KB * 64; e += blockDim.x) {
+        const int t = e >> 6, i = e & 63;
+        const int64_t x = x0 + i;
+        tile[t][i] = (t < k && x < nx) ? T[(int64_t)t * ldT + x] : 0;
+    }
+    __syncthreads();
+    // item = (row i of the tile, stored chunk s): consecutive threads write
+    // consecutive 16-byte chunks of one plane
+    for (int item = threadIdx.x; item < 64 * 8; item += blockDim.x) {
+        const int i = item >> 3, s = item & 7;
+        const int c = s ^ (i & 7);            // logical chunk: residues of t = 16c .. 16c + 15
+        int32_t v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = tile[16 * c + j][i];
+#pragma unroll 1
+        for (int q = 0; q < CRT_L; ++q) {
+            const uint32_t mq = cc.m[q];
+            uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                uint32_t r = small_mod30(v[j], mq, cc.off30[q], cc.mgf[q]);
+                if (SCALE) r = small_mod24(r * cc.y[q], mq, cc.mgc[q]);
+                w[j >> 2] |= ((uint32_t)small_balanced(r, mq) & 255u) << (8 * (j & 3));
+            }
+            *reinterpret_cast<uint4*>(out + ((int64_t)q * x_pad + x0 + i) * CRT_KB + 16 * s) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The tensor-core update
+
+__device__ __forceinline__ void mma_s8(int (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                       uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up (false) after about
+// `limit` SM clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (clock64() - t0 < limit)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(CRT_THREADS, 2)
+update_crt_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, int c0, Field f,
+                  const DenseState* __restrict__ st, const uint8_t* __restrict__ Fr,
+                  const uint8_t* __restrict__ Rr, int64_t m_pad, int64_t n_pad,
+                  const int32_t* __restrict__ R, int64_t ldR, CrtConsts cc, int* status, long long spin) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ int s_fail;
+    const int k = st->k;
+    if (k == 0) return;
+    const int r = st->r;
+    const int ksteps = (k + 31) / 32;
+    const int64_t row0 = (int64_t)blockIdx.y * CRT_BM;
+    const int64_t col0 = (int64_t)blockIdx.x * CRT_BN;
+    const int64_t ncols = n - c0;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = warp & 1, wn = warp >> 1;        // 2 x 4 warps of 32 x 16 outputs
+    const int g = lane >> 2, t4 = lane & 3;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t bar0 = sbase + CRT_STAGES * CRT_STAGE_BYTES;
+
+    if (tid == 0) {
+        for (int s = 0; s < CRT_STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int q) {   // residues of modulus q into stage q % CRT_STAGES
+        const int s = q % CRT_STAGES;
+        const uint32_t bar = bar0 + 8 * s;
+        const uint32_t dst = sbase + s * CRT_STAGE_BYTES;
+        mbar_expect_tx(bar, CRT_STAGE_BYTES);
+        bulk_load(dst, Fr + ((int64_t)q * m_pad + row0) * CRT_KB, CRT_A_BYTES, bar);
+        bulk_load(dst + CRT_A_BYTES, Rr + ((int64_t)q * n_pad + col0) * CRT_KB, CRT_B_BYTES, bar);
+    };
+    int issued = 0;   // loads issued so far (thread 0 only)
+    if (tid == 0)
+        for (; issued < CRT_STAGES; ++issued) issue(issued);
+
+    uint32_t S[2][2][4];
+    uint64_t X[2][2][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                S[a][b][e] = 0;
+                X[a][b][e] = 0;
+            }
+
+    // byte offsets of this thread's fragments inside a stage (the swizzle
+    // uses row & 7 = g for every row and column the thread touches)
+    const int arow = (wm * 32 + g) * CRT_KB + 4 * t4;
+    const int bcol = (wn * 16 + g) * CRT_KB + 4 * t4;
+    bool failed = false;
+    int q = 0;
+
+#pragma unroll 1
+    for (; q < CRT_L; ++q) {
+        const int s = q % CRT_STAGES;
+        if (!mbar_wait(bar0 + 8 * s, (uint32_t)((q / CRT_STAGES) & 1), spin)) failed = true;
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
+        const uint8_t* As = smem + s * CRT_STAGE_BYTES;
+        const uint8_t* Bs = As + CRT_A_BYTES;
+        int D[2][2][4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) D[a][b][e] = 0;
+#pragma unroll 1
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int c_lo = ((2 * ks) ^ g) * 16, c_hi = ((2 * ks + 1) ^ g) * 16;
+            uint32_t af[2][4], bf[2][2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const uint8_t* p0 = As + arow + a * 16 * CRT_KB;
+                af[a][0] = *reinterpret_cast<const uint32_t*>(p0 + c_lo);
+                af[a][1] = *reinterpret_cast<const uint32_t*>(p0 + 8 * CRT_KB + c_lo);
+                af[a][2] = *reinterpret_cast<const uint32_t*>(p0 + c_hi);
+                af[a][3] = *reinterpret_cast<const uint32_t*>(p0 + 8 * CRT_KB + c_hi);
+            }
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const uint8_t* p0 = Bs + bcol + b * 8 * CRT_KB;
+                bf[b][0] = *reinterpret_cast<const uint32_t*>(p0 + c_lo);
+                bf[b][1] = *reinterpret_cast<const uint32_t*>(p0 + c_hi);
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) mma_s8(D[a][b], af[a][0], af[a][1], af[a][2], af[a][3], bf[b][0], bf[b][1]);
+        }
+        __syncthreads();   // every warp has read stage s: it may be refilled
+        if (tid == 0 && issued < CRT_L) issue(issued++);
+        // step 3 for modulus q
+        const uint32_t mq = cc.m[q], off = cc.off21[q], mgc = cc.mgc[q], w16 = cc.w16[q], wp = cc.wp[q];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t t = small_mod24((uint32_t)D[a][b][e] + off, mq, mgc);
+                    S[a][b][e] += t * w16;
+                    X[a][b][e] += (uint64_t)t * wp;
+                }
+    }
+    if (failed) {
+        // wait (bounded) for the copies still in flight into this block's
+        // buffers (loads q .. issued - 1), then report and leave
+        if (tid == 0) {
+            atomicCAS(status, 0, (int)LINAC_ERR_TIMEOUT);
+            for (int j = q; j < issued; ++j)
+                (void)mbar_wait(bar0 + 8 * (j % CRT_STAGES), (uint32_t)((j / CRT_STAGES) & 1), spin);
+        }
+        __syncthreads();
+        return;
+    }
+
+    // step 4 and the write-back: rows of the new pivot block receive R,
+    // every other row C - D mod p
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int64_t row = row0 + wm * 32 + a * 16 + g + hh * 8;
+            if (row >= m) continue;
+            const bool pivot_row = row >= r && row < r + k;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int64_t col = col0 + wn * 16 + b * 8 + 2 * t4;
+                if (col >= ncols) continue;
+                uint32_t out[2];
+                uint32_t* dst = M + row * ld + c0 + col;
+                const bool pair = col + 1 < ncols;
+                if (pivot_row) {
+                    const int32_t* rr = R + (int64_t)(row - r) * ldR + col;
+                    out[0] = from_balanced(rr[0], f);
+                    out[1] = pair ? from_balanced(rr[1], f) : 0u;
+                } else {
+                    uint32_t cval[2];
+                    if (pair) {
+                        const uint2 cv = *reinterpret_cast<const uint2*>(dst);
+                        cval[0] = cv.x;
+                        cval[1] = cv.y;
+                    } else {
+                        cval[0] = dst[0];
+                        cval[1] = 0;
+                    }
+#pragma unroll
+                    for (int qq = 0; qq < 2; ++qq) {
+                        const int e = hh * 2 + qq;
+                        const uint32_t alpha = (S[a][b][e] + 32768u) >> 16;
+                        const uint64_t x = X[a][b][e] + (uint64_t)alpha * cc.negMp;
+                        out[qq] = submod(cval[qq], reduce64(x, f), f);
+                    }
+                }
+                if (pair) *reinterpret_cast<uint2*>(dst) = make_uint2(out[0], out[1]);
+                else dst[0] = out[0];
+            }
+        }
+}
+
+linac_status launch_update_crt(uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0, const Field& f,
+                               const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,
+                               int64_t ldR, const CrtScratch* crt, int* status, cudaStream_t stream) {
+    if (!crt) return LINAC_ERR_ARG;
+    const int64_t ncols = n - c0;
+    if (ncols <= 0 || m <= 0) return LINAC_OK;
+    const CrtConsts cc = make_crt(f.p);
+    {
+        ProfScope ps(stream, PROF_CRT_SPLIT);
+        crt_split_kernel<false><<<(unsigned)(crt->m_pad / 64), 256, 0, stream>>>(Ft, ldF, m, st, cc, crt->Fr,
+                                                                                crt->m_pad);
+        crt_split_kernel<true><<<(unsigned)((ncols + 63) / 64), 256, 0, stream>>>(R, ldR, ncols, st, cc, crt->Rr,
+                                                                                 crt->n_pad);
+    }
+    LINAC_CUDA_TRY(cudaFuncSetAttribute(update_crt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)CRT_SMEM));
+    dim3 grid((unsigned)((ncols + CRT_BN - 1) / CRT_BN), (unsigned)((m + CRT_BM - 1) / CRT_BM));
+    {
+        ProfScope ps(stream, PROF_UPDATE_CRT);
+        update_crt_kernel<<<grid, CRT_THREADS, CRT_SMEM, stream>>>(M, m, n, ld, c0, f, st, crt->Fr, crt->Rr,
+                                                                   crt->m_pad, crt->n_pad, R, ldR, cc, status,
+                                                                   wait_limit().spin_cycles);
+    }
+    LINAC_CUDA_TRY(cudaGetLastError());
+    return LINAC_OK;
+}
+
+size_t crt_scratch_bytes(int64_t m, int64_t n) {
+    const int64_t m_pad = (std::max<int64_t>(m, 1) + CRT_BM - 1) / CRT_BM * CRT_BM;
+    const int64_t n_pad = (std::max<int64_t>(n, 1) + CRT_BN - 1) / CRT_BN * CRT_BN;
+    return (size_t)CRT_L * (size_t)(m_pad + n_pad) * CRT_KB;
+}
+
+void crt_scratch_layout(void* base, int64_t m, int64_t n, CrtScratch* out) {
+    out->m_pad = (std::max<int64_t>(m, 1) + CRT_BM - 1) / CRT_BM * CRT_BM;
+    out->n_pad = (std::max<int64_t>(n, 1) + CRT_BN - 1) / CRT_BN * CRT_BN;
+    out->Fr = (uint8_t*)base;
+    out->Rr = (uint8_t*)base + (size_t)CRT_L * out->m_pad * CRT_KB;
+}
+
+}  // namespace linac

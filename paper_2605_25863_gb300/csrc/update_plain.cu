@@ -176,12 +176,18 @@ linac_status launch_update_limb(uint32_t* M, int64_t m, int64_t n, int64_t ld, i
                                 const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,
                                 int64_t ldR, const LimbScratch* limb, cudaStream_t stream);
 
+linac_status launch_update_crt(uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0, const Field& f,
+                               const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,
+                               int64_t ldR, const CrtScratch* crt, int* status, cudaStream_t stream);
+
 linac_status launch_update(int path, uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0,
                            const Field& f, const DenseState* st, const int32_t* Ft, int64_t ldF,
                            const int32_t* R, int64_t ldR, const LimbScratch* limb,
-                           cudaStream_t stream) {
+                           const CrtScratch* crt, int* status, cudaStream_t stream) {
     if (path == LINAC_PATH_LIMB)
         return launch_update_limb(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, limb, stream);
+    if (path == LINAC_PATH_CRT)
+        return launch_update_crt(M, m, n, ld, c0, f, st, Ft, ldF, R, ldR, crt, status, stream);
     const int64_t ncols = n - c0;
     if (ncols <= 0 || m <= 0) return LINAC_OK;
     dim3 grid((unsigned)((ncols + UPD_BN2 - 1) / UPD_BN2), (unsigned)((m + UPD_BM - 1) / UPD_BM));

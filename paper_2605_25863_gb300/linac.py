@@ -20,9 +20,9 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-LINAC_PATH_AUTO, LINAC_PATH_PLAIN, LINAC_PATH_LIMB = 0, 1, 2
+LINAC_PATH_AUTO, LINAC_PATH_PLAIN, LINAC_PATH_LIMB, LINAC_PATH_CRT = 0, 1, 2, 3
 LINAC_SHARED_PATTERN = 1
-_PATHS = {"auto": LINAC_PATH_AUTO, "plain": LINAC_PATH_PLAIN, "limb": LINAC_PATH_LIMB}
+_PATHS = {"auto": LINAC_PATH_AUTO, "plain": LINAC_PATH_PLAIN, "limb": LINAC_PATH_LIMB, "crt": LINAC_PATH_CRT}
 
 
 class LinacError(RuntimeError):
@@ -35,13 +35,6 @@ class LinacError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("nb", ctypes.c_int32),
                 ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32)]
-
-
-class IntRates(ctypes.Structure):
-    _fields_ = [("imad_wide_per_s", ctypes.c_double), ("imma_u8_mac_per_s", ctypes.c_double),
-                ("dp4a_u8_mac_per_s", ctypes.c_double), ("sm_clock_khz", ctypes.c_double),
-                ("sm_count", ctypes.c_int), ("coissue_imad_only_ms", ctypes.c_double),
-                ("coissue_imma_only_ms", ctypes.c_double), ("coissue_both_ms", ctypes.c_double)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -83,8 +76,6 @@ def lib():
         L.linac_profile_reset.restype = None
         L.linac_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), ctypes.c_int]
         L.linac_profile_read.restype = ctypes.c_int
-        L.linac_measure_int_rates.argtypes = [ctypes.POINTER(IntRates), vp]
-        L.linac_measure_int_rates.restype = ctypes.c_int
         L.linac_batched_tune.argtypes = [ctypes.c_uint32, ctypes.c_void_p, vp]
         L.linac_batched_tune.restype = ctypes.c_int
         L.linac_batched_panel_widths.argtypes = [ctypes.c_void_p]
@@ -103,6 +94,10 @@ def lib():
         L.linac_solve64.argtypes = [vp, i64, i64, i64, vp, i64, i64, u64, vp, i64, vp, vp, vp, vp]
         L.linac_null_space64.argtypes = [vp, i64, i64, i64, vp, vp, u64, vp, i64, i64, vp, vp, vp]
         L.linac_rank_factor64.argtypes = [vp, i64, i64, i64, vp, vp, vp, i64, i64, vp]
+        L.linac_set_wait_limit.argtypes = [i64]
+        L.linac_set_wait_limit.restype = ctypes.c_int
+        L.linac_debug_inject_wait_failure.argtypes = [i32]
+        L.linac_debug_inject_wait_failure.restype = None
         L.linac_workspace64_bytes.argtypes = [i64, i64]
         L.linac_workspace64_bytes.restype = ctypes.c_size_t
         for name in ("linac_rref", "linac_rref_ex", "linac_solve", "linac_solve_ex",
@@ -316,6 +311,17 @@ def linac_last_device_status(stream=None) -> int:
     return int(lib().linac_last_device_status(_stream_ptr(stream)))
 
 
+def linac_set_wait_limit(cycles: int) -> None:
+    """Limit of the device-side waits in SM clock cycles (0 = default, ~2 s)."""
+    _check(lib().linac_set_wait_limit(int(cycles)), "linac_set_wait_limit")
+
+
+def linac_debug_inject_wait_failure(on: bool) -> None:
+    """Test support: while on, the full-height pivot search's arrival barrier
+    can never complete, so its waits run out (LINAC_ERR_TIMEOUT)."""
+    lib().linac_debug_inject_wait_failure(1 if on else 0)
+
+
 def linac_workspace_bytes(m: int, n: int, nb: int = 0) -> int:
     o = _opts("auto", nb, False)
     return int(lib().linac_workspace_bytes(m, n, ctypes.byref(o)))
@@ -342,13 +348,6 @@ def linac_profile_read() -> dict:
 
 def linac_launch_count() -> int:
     return int(lib().linac_launch_count())
-
-
-def linac_measure_int_rates(stream=None) -> dict:
-    """Measured integer pipe rates of the current device (see include/linac.h)."""
-    r = IntRates()
-    _check(lib().linac_measure_int_rates(ctypes.byref(r), _stream_ptr(stream)), "linac_measure_int_rates")
-    return {k: getattr(r, k) for k, _ in IntRates._fields_}
 
 
 def linac_batched_tune(p: int, stream=None) -> list[int]:

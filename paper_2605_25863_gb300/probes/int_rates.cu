@@ -1,17 +1,21 @@
-// diag.cu -- throughput probes for the roofline denominators of the two
+// int_rates.cu -- throughput probes for the roofline denominators of the
 // trailing-update paths: the integer multiply-add pipe (mad.wide.s32, the
 // instruction of the plain path) and the integer tensor pipe
-// (mma.sync m16n8k32 u8 -> s32, the instruction of the limb path), plus dp4a
-// for comparison.  Each probe keeps many independent chains in flight so the
+// (mma.sync m16n8k32 u8 -> s32 of the limb path, s8 -> s32 of the
+// multi-modular path), plus dp4a for comparison.
+//
+// Measurement tooling only: built into its own library, liblinac_probes.so,
+// which the benchmark loads for --measure-peaks; liblinac.so does not
+// contain it.  Each probe keeps many independent chains in flight so the
 // pipe, not latency, is the limit, and feeds every multiply an operand that
 // changes each iteration (a loop-invariant product could be hoisted by the
 // compiler, turning the probe into an add-throughput probe).
+#include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/linac.h"
-#include "linac_host.h"
+#include "int_rates.h"
 
-namespace linac {
+namespace linac_probes {
 
 __global__ void probe_imad_wide(unsigned long long* out, uint32_t seed, int iters) {
     long long acc[8];
@@ -66,6 +70,26 @@ __global__ void probe_imma_u8(int* out, uint32_t seed, int iters) {
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void probe_imma_s8(int* out, uint32_t seed, int iters) {
+    const uint32_t a0 = seed ^ threadIdx.x, a1 = a0 * 3, a2 = a0 * 5, a3 = a0 * 7, b0 = a0 * 11, b1 = a0 * 13;
+    int d[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) d[c][0] = d[c][1] = d[c][2] = d[c][3] = 0;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            asm volatile(
+                "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+r"(d[c][0]), "+r"(d[c][1]), "+r"(d[c][2]), "+r"(d[c][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+    int s = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) s += d[c][0] + d[c][1] + d[c][2] + d[c][3];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // Co-issue: warps 0-7 run mad.wide.s32 chains (multiply pipe), warps 8-15
 // run mma.sync u8 (tensor pipe).  MODE 0: only the first group works,
 // 1: only the second, 2: both at once.
@@ -109,16 +133,19 @@ __global__ void __launch_bounds__(512, 1) probe_coissue(long long* out, int it_i
     out[blockIdx.x * 512 + threadIdx.x] = s;
 }
 
-}  // namespace linac
+}  // namespace linac_probes
 
-using namespace linac;
+using namespace linac_probes;
 
-extern "C" linac_status linac_measure_int_rates(linac_int_rates* out, cudaStream_t stream) {
-    if (!out) return LINAC_ERR_ARG;
-    const int nsm = sm_count();
+extern "C" int linac_probe_int_rates(linac_int_rates* out, cudaStream_t stream) {
+    if (!out) return 1;
+    int dev = 0, nsm = 0, clk = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 4;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) return 4;
+    cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
     const int grid = nsm * 8, threads = 256, iters = 4096;
     void* buf = nullptr;
-    LINAC_CUDA_TRY(cudaMalloc(&buf, (size_t)grid * threads * 8));   // >= nsm * 512 * 8 for the co-issue probe
+    if (cudaMalloc(&buf, (size_t)grid * threads * 8) != cudaSuccess) return 5;   // >= nsm * 512 * 8 for the co-issue probe
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -139,6 +166,8 @@ extern "C" linac_status linac_measure_int_rates(linac_int_rates* out, cudaStream
     out->dp4a_u8_mac_per_s = lanes * iters * 8 * 4 / t;
     t = time_it([&](int it) { probe_imma_u8<<<grid, threads, 0, stream>>>((int*)buf, 1u, it); });
     out->imma_u8_mac_per_s = (double)grid * (threads / 32) * iters * 4 * 4096.0 / t;
+    t = time_it([&](int it) { probe_imma_s8<<<grid, threads, 0, stream>>>((int*)buf, 1u, it); });
+    out->imma_s8_mac_per_s = (double)grid * (threads / 32) * iters * 4 * 4096.0 / t;
     {
         // co-issue of the two pipes in one block per SM
         const int ii = 2048, im = 1024;
@@ -149,13 +178,11 @@ extern "C" linac_status linac_measure_int_rates(linac_int_rates* out, cudaStream
         out->coissue_both_ms =
             1e3 * time_it([&](int) { probe_coissue<2><<<nsm, 512, 0, stream>>>((long long*)buf, ii, im); });
     }
-    int clk = 0;
-    cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
     out->sm_clock_khz = clk;
     out->sm_count = nsm;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaError_t e = cudaGetLastError();
     cudaFree(buf);
-    return e == cudaSuccess ? LINAC_OK : LINAC_ERR_CUDA;
+    return e == cudaSuccess ? 0 : 4;
 }

@@ -21,6 +21,15 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, s), f"{s} declared in include/linac.h but not exported"
 
 
+def test_probes_live_in_their_own_library(lib):
+    """The pipe-rate probes are measurement tooling: exported by
+    liblinac_probes.so, not by liblinac.so."""
+    assert not hasattr(lib, "linac_measure_int_rates")
+    assert not hasattr(lib, "linac_probe_int_rates")
+    probes = ctypes.CDLL(build.PROBES_LIB)
+    assert hasattr(probes, "linac_probe_int_rates")
+
+
 def test_build_targets_sm_103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -57,7 +66,7 @@ def test_misaligned_pointer_rejected(lib):
 def test_bad_options_rejected(lib):
     rank = ctypes.c_int32()
     piv = (ctypes.c_int32 * 8)()
-    for path, nb in ((3, 0), (-1, 0), (0, 20), (0, 256)):
+    for path, nb in ((4, 0), (-1, 0), (0, 20), (0, 256)):
         o = linac.Options(path, nb, 0, 0)
         assert lib.linac_rref_ex(ctypes.c_void_p(0x1000), 4, 4, 4, 2**31 - 1, 4, ctypes.byref(rank), piv,
                                  ctypes.byref(o), None) == 1

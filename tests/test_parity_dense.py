@@ -48,7 +48,7 @@ def test_uniform_vs_oracle(shape, p):
 
 
 @pytest.mark.parametrize("nb", [16, 32, 64, 128])
-@pytest.mark.parametrize("path", ["plain", "auto", "limb"])
+@pytest.mark.parametrize("path", ["plain", "auto", "limb", "crt"])
 def test_panel_widths(nb, path):
     M, _ = synth.rank_deficient(m=333, n=401, d=21, p=P31, seed=nb)
     check_against_oracle(M, P31, nb=nb, path=path)
@@ -206,3 +206,43 @@ def test_pivot_window_fallback(p, zero_rows):
     M[:zero_rows // 2, 140] = 0
     check_against_oracle(M, p)
     check_against_oracle(M, p, nb=32)
+
+
+@pytest.mark.parametrize("p", [3, 251, 65537, P31, PB, 1431655777, 1908903247])
+@pytest.mark.parametrize("shape", [(37, 45), (300, 300), (513, 700), (1000, 1100)])
+def test_crt_path_vs_oracle(shape, p):
+    """The multi-modular integer-tensor update (nine s8 residue GEMMs and an
+    exact Chinese-remainder reconstruction) gives the oracle's RREF."""
+    m, n = shape
+    M = synth.uniform(shape, p, synth.stream_key(m * 37 + n, f"crt{p}"))
+    check_against_oracle(M, p, path="crt")
+
+
+@pytest.mark.parametrize("nb", [16, 64, 128])
+def test_crt_path_rank_deficient(nb):
+    M, _ = synth.rank_deficient(m=700, n=650, d=33, p=PB, seed=nb + 200)
+    check_against_oracle(M, PB, path="crt", nb=nb)
+
+
+@pytest.mark.parametrize("p", [P31, PB, 1431655777, 251])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_crt_path_extreme_products(p, sign):
+    """The reconstruction's worst case: A = [[I, X], [Y, Z]] with a 128 x 128
+    identity, so the first panel's pivot rows are [I | X] unchanged and its
+    update subtracts Y X; with every entry of X and Y at the balanced extreme
+    (p - 1)/2 (or -(p - 1)/2 in X) each output is +-128 ((p - 1)/2)^2, the
+    largest |F R| a 128-column panel can produce."""
+    half = (p - 1) // 2
+    m, n = 600, 640
+    M = synth.uniform((m, n), p, synth.stream_key(p % 1000 + sign, "crt_extreme"))
+    M[:128, :128] = np.eye(128, dtype=np.uint32)
+    M[:128, 128:] = half if sign > 0 else half + 1
+    M[128:, :128] = half
+    check_against_oracle(M, p, path="crt", nb=128)
+
+
+def test_crt_and_plain_agree_on_workload_4096():
+    M, _ = synth.rank_deficient()
+    Rc, rc, pc = gpu_rref(M, P31, path="crt")
+    Rp, rp, pp = gpu_rref(M, P31, path="plain")
+    assert rc == rp == 4032 and np.array_equal(pc, pp) and np.array_equal(Rc, Rp)
