@@ -62,6 +62,8 @@ def _load():
         lib.oracle_matmul.argtypes = [vp, i64, i64, i64, vp, i64, i64, u32, vp, i64]
         lib.oracle_matmul.restype = ctypes.c_int
         u64 = ctypes.c_uint64
+        lib.oracle_lup.argtypes = [vp, i64, i64, i64, u32, vp, i64, vp, i64, i32p, i32p, i32p, vp, vp, vp]
+        lib.oracle_lup.restype = ctypes.c_int
         lib.oracle_rref64.argtypes = [vp, i64, i64, i64, u64, i64, ctypes.c_int, i32p, i32p]
         lib.oracle_rref64.restype = ctypes.c_int
         lib.oracle_solve64.argtypes = [vp, i64, i64, i64, i64, u64, ctypes.c_int, vp, i64, vp, i32p, i32p]
@@ -144,6 +146,36 @@ def solve(A, B, p: int, nthreads: int = 1):
         raise ValueError("oracle_solve rejected its arguments")
     return (X[:nA, :k].copy(), cons[:k].astype(bool), int(rank.value),
             piv[: rank.value].copy(), M)
+
+
+def lup(A, p: int):
+    """LUP factorisation P A = L U (the option paper section 6 names beside
+    the rank decomposition; see oracle_lup in oracle.c for the reading).
+
+    Returns (L, U, perm, rank, pivots): L is m x min(m, n) (the first columns
+    of the unit lower triangular factor), U is m x n in row-echelon form (rows
+    at and beyond the rank zero), row i of P A is row perm[i] of A, and pivots
+    (length rank) are the pivot columns.
+    """
+    A = _as_matrix(A)
+    m, n = A.shape
+    mn = min(m, n)
+    L = np.zeros((m, max(mn, 1)), dtype=np.uint32)
+    U = np.zeros((m, max(n, 1)), dtype=np.uint32)
+    perm = np.zeros(max(m, 1), dtype=np.int32)
+    piv = np.full(max(mn, 1), -1, dtype=np.int32)
+    W = np.zeros(max(m * n, 1), dtype=np.uint32)
+    Lo = np.zeros(max(m * mn, 1), dtype=np.uint32)
+    isp = np.zeros(max(m, 1), dtype=np.uint8)
+    rank = ctypes.c_int32(0)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    rc = _load().oracle_lup(A.ctypes.data, m, n, n, p, L.ctypes.data, L.shape[1], U.ctypes.data, U.shape[1],
+                            perm.ctypes.data_as(i32p), ctypes.byref(rank), piv.ctypes.data_as(i32p),
+                            W.ctypes.data, Lo.ctypes.data, isp.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_lup rejected its arguments")
+    r = int(rank.value)
+    return L[:, :mn].copy(), U[:, :n].copy(), perm[:m].copy(), r, piv[:r].copy()
 
 
 def null_space(R: np.ndarray, pivots: np.ndarray, p: int) -> np.ndarray:

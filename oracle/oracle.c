@@ -279,6 +279,82 @@ int oracle_matmul(const uint32_t *A, int64_t m, int64_t K, int64_t lda,
     return 0;
 }
 
+/*
+ * LUP factorisation P A = L U (paper section 6, "Conclusions and Outlook",
+ * names an LUP factorisation as the option to add beside the rank
+ * decomposition; the paper does not define it further, so this is the
+ * reading the library implements).  The elimination is the column loop of
+ * section 3.2 with two changes: only the rows that are not yet pivots are
+ * reduced (no "Row reduce" of the rows above, no rescaling of the pivot row),
+ * and the multiplier f / h of every reduced row is kept in L.  The pivot of
+ * column c is the lowest-index row, in the ORIGINAL order, among the rows that
+ * are not yet pivots and have a nonzero entry in column c ("Pivoting": any
+ * nonzero entry will do; this rule makes P, L and U unique).  With r the rank:
+ *   perm[t] (t < r)   the pivot row of the t-th pivot column pivots[t];
+ *   perm[r..m-1]      the other rows in increasing order;
+ *   U (m x n)         row t < r is row perm[t] after the elimination (zero
+ *                     left of pivots[t], head U[t][pivots[t]] != 0); rows
+ *                     r..m-1 are zero;
+ *   L (m x min(m,n))  the first min(m,n) columns of the m x m unit lower
+ *                     triangular factor: L[i][i] = 1, L[i][t] for i > t, t < r
+ *                     is the multiplier row perm[i] took for pivot t, and
+ *                     column t >= r is the unit vector e_t.
+ * Row i of P A is row perm[i] of A.  Every product is reduced with '%'.
+ * The work matrix W (m x n, leading dimension n) and Lo (m x min(m,n)) are
+ * caller-provided scratch.  Returns 0, or -1 for bad arguments.
+ */
+int oracle_lup(const uint32_t *A, int64_t m, int64_t n, int64_t ld, uint32_t p,
+               uint32_t *L, int64_t ldl, uint32_t *U, int64_t ldu,
+               int32_t *perm, int32_t *rank, int32_t *pivots,
+               uint32_t *W, uint32_t *Lo, uint8_t *is_pivot) {
+    if (m < 0 || n < 0 || ld < n || p < 2) return -1;
+    const int64_t mn = m < n ? m : n;
+    if (ldl < mn || ldu < n) return -1;
+    for (int64_t i = 0; i < m; i++) {
+        is_pivot[i] = 0;
+        for (int64_t j = 0; j < n; j++) W[i * n + j] = A[i * ld + j];
+        for (int64_t t = 0; t < mn; t++) Lo[i * mn + t] = 0;
+    }
+    for (int64_t t = 0; t < mn; t++) pivots[t] = -1;
+    int64_t r = 0;
+    for (int64_t c = 0; c < n && r < m; c++) {
+        int64_t q = -1;
+        for (int64_t i = 0; i < m; i++)
+            if (!is_pivot[i] && W[i * n + c] != 0) { q = i; break; }
+        if (q < 0) continue;
+        const uint64_t hinv = oracle_inverse(W[q * n + c], p);
+        for (int64_t i = 0; i < m; i++) {
+            if (is_pivot[i] || i == q) continue;
+            const uint64_t f = W[i * n + c];
+            if (f == 0) continue;
+            const uint64_t l = (f * hinv) % p;
+            Lo[i * mn + r] = (uint32_t)l;
+            const uint64_t negl = p - l;
+            for (int64_t j = c; j < n; j++)
+                W[i * n + j] = (uint32_t)(((uint64_t)W[i * n + j] + negl * (uint64_t)W[q * n + j]) % p);
+        }
+        is_pivot[q] = 1;
+        perm[r] = (int32_t)q;
+        pivots[r] = (int32_t)c;
+        r++;
+    }
+    *rank = (int32_t)r;
+    int64_t t = r;
+    for (int64_t i = 0; i < m; i++)
+        if (!is_pivot[i]) perm[t++] = (int32_t)i;
+    for (int64_t i = 0; i < m; i++) {
+        for (int64_t s = 0; s < mn; s++) {
+            uint32_t v;
+            if (s == i) v = 1;
+            else if (s < i && s < r) v = Lo[(int64_t)perm[i] * mn + s];
+            else v = 0;
+            L[i * ldl + s] = v;
+        }
+        for (int64_t j = 0; j < n; j++) U[i * ldu + j] = i < r ? W[(int64_t)perm[i] * n + j] : 0;
+    }
+    return 0;
+}
+
 /* ===========================================================================
  * 64-bit residues.  Section 2.3 ("Basic Usage"): residues are held as uint64
  * when p does not fit 32 bits, for primes up to 2^64 - 1 (and section 3.4,

@@ -54,14 +54,25 @@ MUTANTS64 = {
                                       "return (uint64_t)((a * b) % p);"),
 }
 
+# planted slips in the LUP factorisation, caught by its pins
+LUP_MUTANTS = {
+    "lup_multiplier_not_divided_by_head": ("const uint64_t l = (f * hinv) % p;", "const uint64_t l = f % p;"),
+    "lup_reduces_earlier_pivot_rows": ("if (is_pivot[i] || i == q) continue;", "if (i == q) continue;"),
+    "lup_pivot_is_last_candidate": ("if (!is_pivot[i] && W[i * n + c] != 0) { q = i; break; }",
+                                    "if (!is_pivot[i] && W[i * n + c] != 0) { q = i; }"),
+    "lup_other_rows_reversed": ("for (int64_t i = 0; i < m; i++)\n        if (!is_pivot[i]) perm[t++]",
+                                "for (int64_t i = m - 1; i >= 0; i--)\n        if (!is_pivot[i]) perm[t++]"),
+}
+
 PIN_FILES = {**{k: "test_oracle_pins.py" for k in MUTANTS},
+             **{k: "test_oracle_lup.py" for k in LUP_MUTANTS},
              **{k: "test_oracle_construction.py" for k in CONSTRUCTION_MUTANTS},
              **{k: "test_oracle64_pins.py" for k in MUTANTS64}}
 
 
 @pytest.mark.parametrize("name", sorted(PIN_FILES))
 def test_pins_fail_on_mutant(name, tmp_path):
-    before, after = {**MUTANTS, **CONSTRUCTION_MUTANTS, **MUTANTS64}[name]
+    before, after = {**MUTANTS, **CONSTRUCTION_MUTANTS, **MUTANTS64, **LUP_MUTANTS}[name]
     pins = PIN_FILES[name]
     src = open(SRC).read()
     assert src.count(before) == 1, f"mutation site for {name} not found exactly once"
