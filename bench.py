@@ -365,6 +365,8 @@ def run_ours(args):
     rank_v = int(events[-1][2].item())
     piv = events[-1][3].cpu().numpy()[:rank_v]
     ok = rank_v == m and np.array_equal(piv, np.arange(m))
+    content = content_check(linac, pristine, work, m, p) if ok else {"checked": False}
+    ok = ok and content.get("identity_block", False) and content.get("freivalds", False)
     work_macs = gj_work(m, n, piv)
     value, tot_ms = replica_rate(sum(step_ms), work_macs * args.steps, world, dev)
 
@@ -381,6 +383,10 @@ def run_ours(args):
         traffic = UPDATE_BYTES_PER_OUTPUT * update_outputs(m, n, nb) * args.steps / upd_launches
     sms, sm_max_mhz, clk_src = device_sms_and_max_clock(dev)
     peak = sms * IMAD_WIDE_PER_SM_CLK * sm_max_mhz * 1e6 / imad_per_mac
+    s8_peak, u8_peak = imma_peak()
+    peaks = {"plain": peak, "plain_basis": f"{sms} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x "
+                                           f"{sm_max_mhz:.0f} MHz / {imad_per_mac:.3f} per field MAC",
+             "imma_s8": s8_peak, "imma_u8": u8_peak}
     kernel_times = {k: {"launches": v[0], "total_ms": round(v[1], 3),
                         "share": round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4)}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -406,13 +412,16 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "correct": bool(ok),
+        "correct_checks": content,
         "wall_s_timed": t_wall,
         "kernel_times": kernel_times,
     }
 
     if rank == 0 and not args.no_extras:
         line["e2e"] = e2e_leg(args, linac, synth, pristine, work, m, n, p, nb, stream, staging)
-        line["paths"] = path_leg(args, linac, pristine, work, m, n, p, nb, stream, value)
+        line["paths"] = path_leg(args, linac, pristine, work, m, n, p, nb, stream, peaks)
+        line["dense_4096"] = dense_4096_leg(args, linac, synth, dev, stream, peaks)
+        line["dense_256"] = dense_256_leg(args, linac, synth, dev)
         if world == 1:
             line["cpu_baseline"] = cpu_leg(args, pristine, m, n, p)
         line["batched"] = batched_leg(args, linac, synth, dev, stream)
@@ -426,74 +435,218 @@ def run_ours(args):
     return 0
 
 
+def content_check(linac, pristine, work, m, p, trials=2):
+    """The reduced matrix, beyond rank and pivots: its left block is exactly
+    the identity ([A | B] reduces to [I | X], section 5.2), and A X = B mod p
+    by Freivalds' test, A (X v) = B v for random v (a wrong X passes a trial
+    with probability <= 1/p), with the products on linac_matmul."""
+    import torch
+    dev = work.device
+    eye_ok = True
+    for r0 in range(0, m, 4096):
+        blk = work[r0:r0 + 4096, :m]
+        nz = int(torch.count_nonzero(blk).item())
+        diag = blk[torch.arange(blk.shape[0], device=dev), torch.arange(r0, r0 + blk.shape[0], device=dev)]
+        eye_ok &= nz == blk.shape[0] and bool((diag == 1).all().item())
+    rhs = work.shape[1] - m
+    g = np.random.default_rng(2026)
+    v = linac.to_device(g.integers(0, p, size=(rhs, trials), dtype=np.int64).astype(np.uint32), dev)
+    xv = linac.linac_matmul(work[:, m:], v, p)
+    lhs = linac.linac_matmul(pristine[:, :m], xv, p)
+    bv = linac.linac_matmul(pristine[:, m:], v, p)
+    torch.cuda.synchronize()
+    return {"checked": True, "identity_block": bool(eye_ok), "freivalds": bool(torch.equal(lhs, bv)),
+            "freivalds_trials": trials}
+
+
 def e2e_leg(args, linac, synth, pristine, work, m, n, p, nb, stream, staging=None):
-    """Through the public API with host buffers: pinned H2D of the input, the
-    RREF, D2H of the reduced matrix and of rank/pivots, every step."""
+    """Through the public API with host buffers: linac_rref_host on the
+    matrix in pinned host memory, which copies it to the device, reduces it
+    and copies the RREF, rank and pivots back, every step (host wall clock
+    around the call and the stream synchronisation).  The pinned input is
+    restored from a pinned pristine copy before each step, outside the
+    timed region."""
     import torch
     if staging is not None:
-        host_in, host_out = staging
+        host_src, host_io = staging
     else:
-        host_in = torch.empty(pristine.shape, dtype=torch.int32, pin_memory=True)
-        host_out = torch.empty_like(host_in, pin_memory=True)
-    host_in.copy_(pristine)
+        host_src = torch.empty(pristine.shape, dtype=torch.int32, pin_memory=True)
+        host_io = torch.empty_like(host_src, pin_memory=True)
+    host_src.copy_(pristine)
+    rank = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+    piv = torch.full((m,), -1, dtype=torch.int32, pin_memory=True)
     steps = max(1, min(args.steps, 3))
-    parts = []
-
-    def one_step(record):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record(stream)
-        work.copy_(host_in, non_blocking=True)
-        ev[1].record(stream)
-        r, piv = linac.linac_rref(work, p, nb=nb, path=args.path)
-        ev[2].record(stream)
-        host_out.copy_(work, non_blocking=True)
-        ev[3].record(stream)
-        rk = r.to("cpu", non_blocking=True)
-        pv = piv.to("cpu", non_blocking=True)
+    times, parts = [], []
+    for it in range(steps + 2):
+        host_io.copy_(host_src)
+        profiled = it == steps + 1   # one extra call with per-kernel events, for the split
+        if profiled:
+            linac.linac_profile_reset()
+            linac.linac_profile_enable(True)
         torch.cuda.synchronize()
-        if record:
-            parts.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
-        return rk, pv
-
-    one_step(False)   # warm-up: the first transfers through freshly pinned buffers are slower
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        rk, pv = one_step(True)
-    dt = time.perf_counter() - t0
-    macs = gj_work(m, n, pv.numpy()[:int(rk.item())])
-    nbytes = host_in.numel() * 4
-    med = [statistics.median(x[i] for x in parts) for i in range(3)]
-    return {"value": macs * steps / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        t0 = time.perf_counter()
+        linac.linac_rref_host(host_io, p, rank=rank, pivots=piv, stream=stream)
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        if profiled:
+            linac.linac_profile_enable(False)
+            parts.append(linac.linac_profile_read().get("host_copy", (0, 0.0))[1])
+        elif it:   # the first call is the warm-up (it allocates the scratch)
+            times.append(dt)
+    rk = int(rank.item())
+    ok = rk == m and np.array_equal(piv.numpy(), np.arange(m))
+    # the reduced matrix that came back agrees with the device elimination
+    ok = ok and torch.equal(host_io[:4096], work[:4096].cpu())
+    macs = gj_work(m, n, np.arange(rk))
+    nbytes = host_io.numel() * 4
+    dt = statistics.median(times)
+    return {"value": macs / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes + 4 + 4 * m, "steps": steps, "warmup": 1,
-            "ms_per_step": 1000 * dt / steps,
-            "parts_ms": {"h2d": med[0], "rref": med[1], "d2h": med[2]}}
+            "ms_per_step": 1000 * dt, "correct": bool(ok),
+            "api": "linac_rref_host (pinned host matrix; transfers by SM copies inside the call)",
+            "parts_ms": {"copies_in_and_out": parts[0], "rest": 1000 * dt - parts[0]}}
 
 
-def path_leg(args, linac, pristine, work, m, n, p, nb, stream, main_value):
-    """Plain CUDA-core update vs u8-limb integer-tensor update, one timed
-    elimination each (after one warm-up)."""
+def imma_peak():
+    """Measured s8 x s8 -> s32 mma.sync multiply-adds per second of this
+    device (the integer tensor pipe's roofline; probes/int_rates.cu)."""
+    from paper_2605_25863_gb300 import probes
+    r = probes.measure_int_rates()
+    return r["imma_s8_mac_per_s"], r["imma_u8_mac_per_s"]
+
+
+PATH_KERNEL = {"plain": "update_plain", "limb": "update_limb", "crt": "update_crt"}
+# narrow multiply-adds per field multiply-add: u8 limb products (4 x 4) and
+# s8 residue products (nine moduli)
+PATH_NARROW = {"limb": 16, "crt": 9}
+
+
+def time_paths(linac, pristine, work, m, n, p, nb, stream, paths, peaks, reps=2):
+    """One timed elimination per update path (after reps - 1 warm-ups):
+    field MAC/s of the whole elimination and of its update kernel, the
+    latter against the path's roofline (plain: the multiply pipe's
+    mad.wide.s32 rate; limb, crt: the measured tensor-pipe rate of their
+    narrow products)."""
     import torch
     out = {}
-    for path in ("plain", "limb"):
+    for path in paths:
         try:
-            for it in range(2):
+            for it in range(reps):
                 work.copy_(pristine)
+                linac.linac_profile_reset()
+                linac.linac_profile_enable(True)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 r, piv = linac.linac_rref(work, p, nb=nb, path=path)
                 e1.record(stream)
                 torch.cuda.synchronize()
+                linac.linac_profile_enable(False)
+            prof = linac.linac_profile_read()
             ms = e0.elapsed_time(e1)
             rk = int(r.item())
-            macs = gj_work(m, n, piv.cpu().numpy()[:rk])
-            out[path] = {"value": macs / (ms / 1000.0), "ms": ms, "correct": rk == m}
+            pv = piv.cpu().numpy()[:rk]
+            macs = gj_work(m, n, pv)
+            kl, kms = prof.get(PATH_KERNEL[path], (0, 0.0))
+            umacs = update_work(m, n, pv, nb)
+            rate = umacs / (kms / 1e3) if kms else 0.0
+            entry = {"value": macs / (ms / 1000.0), "ms": ms, "rank": rk,
+                     "update_kernel": PATH_KERNEL[path], "update_ms": kms, "update_field_macs_per_s": rate}
+            if path == "plain":
+                entry["roofline"] = {"bound": "alu", "peak": peaks["plain"], "frac": rate / peaks["plain"],
+                                     "unit": "field MAC/s", "basis": peaks["plain_basis"]}
+            else:
+                narrow = PATH_NARROW[path]
+                pk = peaks["imma_u8"] if path == "limb" else peaks["imma_s8"]
+                entry["roofline"] = {"bound": "tensor", "achieved": rate * narrow, "peak": pk,
+                                     "frac": rate * narrow / pk, "unit": "narrow MAC/s",
+                                     "basis": f"{narrow} {'u8' if path == 'limb' else 's8'} products per field "
+                                              f"MAC x update rate / measured mma.sync m16n8k32 rate"}
+            out[path] = entry
         except Exception as e:  # a path that is not available reports why
             out[path] = {"error": str(e)}
-    if "value" in out.get("plain", {}) and "value" in out.get("limb", {}):
-        out["limb_over_plain"] = out["limb"]["value"] / out["plain"]["value"]
     return out
+
+
+def path_leg(args, linac, pristine, work, m, n, p, nb, stream, peaks):
+    """Plain CUDA-core update vs the multi-modular (CRT, nine s8 residue
+    GEMMs) and u8-limb integer-tensor updates on the headline workload."""
+    out = time_paths(linac, pristine, work, m, n, p, nb, stream, ("plain", "crt", "limb"), peaks)
+    for path in ("crt", "limb"):
+        if "value" in out.get("plain", {}) and "value" in out.get(path, {}):
+            out[f"{path}_over_plain"] = out[path]["value"] / out["plain"]["value"]
+    return out
+
+
+def dense_4096_leg(args, linac, synth, dev, stream, peaks):
+    """The 4096 x 4160 system with 64 rows replaced by combinations of others
+    (rank 4032): each update path, elimination time and update-kernel
+    roofline; checked: rank 4032 and pivots 0..4031."""
+    import torch
+    M, _ = synth.rank_deficient()
+    m, n = M.shape
+    pristine = linac.to_device(M, dev)
+    work = linac.padded(m, n, dev)
+    out = time_paths(linac, pristine, work, m, n, P31, 128, stream, ("plain", "crt", "limb"), peaks, reps=3)
+    for path, e in out.items():
+        if "rank" in e:
+            e["correct"] = e["rank"] == 4032
+    out["workload"] = "dense RREF 4096 x 4160, p = 2^31 - 1, 64 rows replaced by combinations (rank 4032)"
+    return out
+
+
+def dense_256_leg(args, linac, synth, dev):
+    """The 256 x 256 system with one right-hand side: [A | b] reduced by
+    linac_rref (one call captured in a CUDA graph, replayed), latency per
+    system; and 1000 such systems in one linac_rref_batched call."""
+    import torch
+    S = synth.dense_system(n=256, k=1, p=P31, seed=1)
+    pristine = linac.to_device(S, dev)
+    A = linac.padded(256, 257, dev)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        rank = torch.zeros(1, dtype=torch.int32, device=dev)
+        piv = torch.full((256,), -1, dtype=torch.int32, device=dev)
+        lib = linac.lib()
+        ptr, mm, nn, ld = linac._matrix(A, "A")
+
+        def call():
+            A.copy_(pristine)
+            code = lib.linac_rref(ptr, mm, nn, ld, P31, rank.data_ptr(), piv.data_ptr(), s.cuda_stream)
+            if code != 0:
+                raise linac.LinacError(code, "linac_rref")
+        call()
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        call()
+    reps = 200
+    with torch.cuda.stream(s):
+        for _ in range(10):
+            g.replay()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            g.replay()
+        e1.record(s)
+    s.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    R = A.cpu().numpy().view(np.uint32)
+    ok = int(rank.item()) == 256 and np.array_equal(R[:, :256], np.eye(256, dtype=np.uint32))
+    # many copies through the batched entry point (independent systems)
+    count = 1000
+    systems = [synth.dense_system(n=256, k=1, p=P31, seed=1 + i) for i in range(count)]
+    B = synth._pack(systems, P31, [256] * count, [0] * count)
+    g2, gs, data, data0, (ranks, pv, poff, st) = _batched_graph(linac, B, dev, 0)
+    ms = _time_graph(g2, data, data0, gs, 3)
+    okb = bool((ranks[:count].cpu().numpy() == 256).all())
+    W = gj_work(256, 257, np.arange(256))
+    return {"workload": "dense RREF of [A | b], A 256 x 256 uniform, p = 2^31 - 1", "us_per_system": us,
+            "systems_per_s": 1e6 / us, "field_macs_per_s": W / (us * 1e-6), "correct": bool(ok),
+            "launch": "linac_rref captured in a CUDA graph, replayed (input restored inside the graph)",
+            "batched": {"systems": count, "ms": ms, "systems_per_s": count / (ms / 1e3), "ranks_ok": okb,
+                        "launch": "linac_rref_batched in a CUDA graph"}}
 
 
 def cpu_leg(args, pristine, m, n, p):

@@ -120,6 +120,29 @@ linac_status linac_rref(uint32_t *d_A, int64_t m, int64_t n, int64_t ld, uint32_
 linac_status linac_rref_noalloc(uint32_t *d_A, int64_t m, int64_t n, int64_t ld, uint32_t p,
                                 int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
 
+/*
+ * linac_rref_host -- linac_rref of a matrix in page-locked HOST memory, with
+ * the transfers inside the call: the matrix is copied to library scratch on
+ * the device, reduced there exactly as linac_rref reduces it (section 3.2;
+ * plain CUDA-core update, default panel width), and copied back in place.
+ *   h_A       m x n, row-major, leading dimension ld (a multiple of 4, start
+ *             16-byte aligned), in page-locked host memory (cudaHostAlloc or
+ *             cudaHostRegister); overwritten by its RREF.
+ *   h_rank    one int32_t, h_pivots min(m, n) int32_t (-1 after the rank):
+ *             also page-locked host memory.
+ * The call is asynchronous on `stream` like every other entry point: read
+ * the outputs after synchronising it.  The copies are made by the SMs
+ * through the host memory's device mapping rather than by the copy engines,
+ * whose host-to-device rate drops after sustained GPU work on GB300.
+ * Scratch: m * ld * 4 bytes plus the pivots, per stream (allocated on first
+ * use as for linac_rref).  The paper has no counterpart (its matrices are
+ * copied to the GPU by the Python layer, section 2.3).
+ * Errors: as linac_rref; LINAC_ERR_ARG also when a pointer is not page-locked
+ * host memory.
+ */
+linac_status linac_rref_host(uint32_t *h_A, int64_t m, int64_t n, int64_t ld, uint32_t p,
+                             int32_t *h_rank, int32_t *h_pivots, cudaStream_t stream);
+
 /* linac_rref with options (NULL = defaults).  ncols_search limits the pivot
  * search to columns [0, ncols_search) while still reducing all n columns
  * (pass n for plain RREF). */

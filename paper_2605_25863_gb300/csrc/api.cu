@@ -193,6 +193,20 @@ WaitLimit wait_limit() {
     return w;
 }
 
+linac_status ensure_dynamic_smem(const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> set;
+    int dev = 0;
+    LINAC_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    int& cur = set[std::make_pair(dev, fn)];
+    if (bytes > cur) {
+        LINAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        cur = bytes;
+    }
+    return LINAC_OK;
+}
+
 int max_smem_optin() { return device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin, g_smem_optin); }
 
 linac_status scratch_get_slot(cudaStream_t stream, int slot, size_t bytes, void** ptr) {

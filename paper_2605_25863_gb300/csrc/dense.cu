@@ -701,10 +701,8 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
     int32_t* W = (int32_t*)(ws + L.off_w);
     int32_t* R = (int32_t*)(ws + L.off_r);
 
-    LINAC_CUDA_TRY(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)psmem));
-    LINAC_CUDA_TRY(cudaFuncSetAttribute(einv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)EINV_SMEM));
+    if ((st_ = ensure_dynamic_smem((const void*)panel_kernel, (int)psmem)) != LINAC_OK) return st_;
+    if ((st_ = ensure_dynamic_smem((const void*)einv_kernel, (int)EINV_SMEM)) != LINAC_OK) return st_;
     int occ = 0;
     LINAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, panel_kernel, PANEL_THREADS, psmem));
     if (occ < 1 || G > occ * sm_count()) return LINAC_ERR_UNSUPPORTED;

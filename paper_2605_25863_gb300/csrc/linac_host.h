@@ -33,7 +33,8 @@ linac_status scratch_get(cudaStream_t stream, size_t bytes, void** ptr);
 // Same, for an independent buffer `slot` (0 = dense elimination, 1 = solve's
 // augmented matrix, 2 = batched driver, 3 = limb planes, 4 = null-space
 // column positions, 6 = uint64 elimination, 7 = the uint64 solve's
-// augmented matrix, 8 = residue planes of the multi-modular update).
+// augmented matrix, 8 = residue planes of the multi-modular update, 9 = the
+// device copy of linac_rref_host's matrix).
 linac_status scratch_get_slot(cudaStream_t stream, int slot, size_t bytes, void** ptr);
 
 // Device status word of the most recent call on this (device, stream): lives
@@ -55,6 +56,12 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // linac_set_wait_limit (kSpinCycles by default) and the injected failure of
 // linac_debug_inject_wait_failure.
 WaitLimit wait_limit();
+
+// cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes) on the current
+// device only when bytes exceeds the value already set there, so repeated
+// calls (and calls made while a stream is being captured) issue no runtime
+// call after the first of each size.
+linac_status ensure_dynamic_smem(const void* fn, int bytes);
 
 // Number of SMs on the current device (cached per device).
 int sm_count();

@@ -12,15 +12,18 @@
 //   2. For each i, D'_i = F_i R'_i on mma.sync m16n8k32 s8 x s8 -> s32 (the
 //      integer MMA of sm_103a; tcgen05 kind::i8 does not exist there).
 //      Exact: |D'_i| <= k * 128^2 <= 2^21.
-//   3. t_i = D'_i mod m_i = (D mod m_i) y_i mod m_i in [0, m_i); then
-//      D = sum_i t_i (M/m_i) - alpha M with the integer alpha that puts D in
-//      (-M/2, M/2).  Because |D|/M < 2^-4.4, alpha is the nearest integer to
-//      sum_i t_i / m_i; it is found in 16-bit fixed point,
-//      S = sum_i t_i floor(2^16 / m_i): S undershoots 2^16 sum_i t_i / m_i by
-//      less than sum_i t_i < 2304, and 2^16 |D|/M < 3146, so
-//      alpha = floor((S + 2^15) / 2^16) exactly.
-//   4. D mod p = (sum_i t_i ((M/m_i) mod p) + alpha ((-M) mod p)) mod p, summed
-//      exactly in 64 bits (< 2^43) and reduced once (Barrett).
+//   3. D'_i = D y_i (mod m_i) and y_i (M/m_i) = 1 (mod m_i), so
+//      sum_i D'_i (M/m_i) = D (mod M), and D = sum_i D'_i (M/m_i) - beta M
+//      for the integer beta that puts D in (-M/2, M/2).  Since |D|/M < 2^-4.4,
+//      beta is the integer nearest to sum_i D'_i / m_i (|beta| < 2^17).  It is
+//      found in fixed point: S = sum_i D'_i floor(2^38 / m_i) differs from
+//      2^38 sum_i D'_i / m_i by less than sum_i |D'_i| <= 9 * 2^21 < 2^25,
+//      and 2^38 |D|/M < 2^34, so beta = floor((S + 2^37) / 2^38) exactly.
+//      No residue is reduced on the way: per modulus and output the step is
+//      two signed 32 x 32 -> 64 multiply-adds (S and X below).
+//   4. D mod p = (X + beta ((-M) mod p)) mod p with X = sum_i D'_i
+//      ((M/m_i) mod p), all exact in signed 64 bits (|X| < 2^56,
+//      |beta ((-M) mod p)| < 2^48) and reduced once.
 // No floating point anywhere.
 //
 // Data: per panel the split kernels write the residue planes Fr[i][row][.]
@@ -32,7 +35,11 @@
 // blocks per SM; the tile's nine (A_i, B_i) pairs (8 KB + 8 KB each) stream
 // through a three-stage ring of shared-memory buffers filled by bulk
 // asynchronous copies (cp.async.bulk, the Blackwell TMA engine) that
-// complete on mbarriers.  Each of the 8 warps computes 32 x 16 outputs.
+// complete on mbarriers.  Each of the 8 warps computes 32 x 16 outputs, and
+// issues the GEMM of modulus i + 1 before folding modulus i into S and X.
+// (Measured and not kept: persistent blocks looping over tiles, and one
+// packed 64-bit accumulator with a per-modulus reduction of D'_i; both were
+// slower.)
 #include <algorithm>
 
 #include "linac_host.h"
@@ -61,10 +68,9 @@ struct CrtConsts {
     uint32_t m[CRT_L];      // the moduli
     uint32_t y[CRT_L];      // (M / m_i)^(-1) mod m_i
     uint32_t off30[CRT_L];  // m_i ceil(2^30 / m_i): makes a balanced residue of p non-negative
-    uint32_t off21[CRT_L];  // m_i ceil(2^21 / m_i): makes D'_i non-negative
     uint32_t mgf[CRT_L];    // floor(2^32 / m_i)
     uint32_t mgc[CRT_L];    // ceil(2^32 / m_i)
-    uint32_t w16[CRT_L];    // floor(2^16 / m_i)
+    uint32_t c38[CRT_L];    // floor(2^38 / m_i) (below 2^31)
     uint32_t wp[CRT_L];     // (M / m_i) mod p
     uint32_t negMp;         // (-M) mod p
 };
@@ -87,10 +93,9 @@ CrtConsts make_crt(uint32_t p) {
             if (Mi_mod * t % mi == 1) { y = t; break; }
         c.y[i] = y;
         c.off30[i] = (uint32_t)(((1ull << 30) + mi - 1) / mi * mi);
-        c.off21[i] = (uint32_t)(((1ull << 21) + mi - 1) / mi * mi);
         c.mgf[i] = (uint32_t)((1ull << 32) / mi);
         c.mgc[i] = (uint32_t)(((1ull << 32) + mi - 1) / mi);
-        c.w16[i] = (uint32_t)((1u << 16) / mi);
+        c.c38[i] = (uint32_t)((1ull << 38) / mi);
         c.wp[i] = (uint32_t)Mi_p;
     }
     const uint64_t Mp = (uint64_t)(M % p);
@@ -213,13 +218,41 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
         : "memory");
 }
 
+// The residue GEMM of one modulus for this thread's 2 x 2 fragments (32 x 16
+// outputs per warp): D += A_q B_q over ksteps k-steps of 32, from one stage.
+__device__ __forceinline__ void crt_mma_stage(int (&D)[2][2][4], const uint8_t* As, const uint8_t* Bs,
+                                              int arow, int bcol, int g, int ksteps) {
+#pragma unroll 1
+    for (int ks = 0; ks < ksteps; ++ks) {
+        const int c_lo = ((2 * ks) ^ g) * 16, c_hi = ((2 * ks + 1) ^ g) * 16;
+        uint32_t af[2][4], bf[2][2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const uint8_t* p0 = As + arow + a * 16 * CRT_KB;
+            af[a][0] = *reinterpret_cast<const uint32_t*>(p0 + c_lo);
+            af[a][1] = *reinterpret_cast<const uint32_t*>(p0 + 8 * CRT_KB + c_lo);
+            af[a][2] = *reinterpret_cast<const uint32_t*>(p0 + c_hi);
+            af[a][3] = *reinterpret_cast<const uint32_t*>(p0 + 8 * CRT_KB + c_hi);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const uint8_t* p0 = Bs + bcol + b * 8 * CRT_KB;
+            bf[b][0] = *reinterpret_cast<const uint32_t*>(p0 + c_lo);
+            bf[b][1] = *reinterpret_cast<const uint32_t*>(p0 + c_hi);
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) mma_s8(D[a][b], af[a][0], af[a][1], af[a][2], af[a][3], bf[b][0], bf[b][1]);
+    }
+}
+
 __global__ void __launch_bounds__(CRT_THREADS, 2)
 update_crt_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, int c0, Field f,
                   const DenseState* __restrict__ st, const uint8_t* __restrict__ Fr,
                   const uint8_t* __restrict__ Rr, int64_t m_pad, int64_t n_pad,
                   const int32_t* __restrict__ R, int64_t ldR, CrtConsts cc, int* status, long long spin) {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int s_fail;
     const int k = st->k;
     if (k == 0) return;
     const int r = st->r;
@@ -236,7 +269,6 @@ update_crt_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, in
     if (tid == 0) {
         for (int s = 0; s < CRT_STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_fail = 0;
     }
     __syncthreads();
     auto issue = [&](int q) {   // residues of modulus q into stage q % CRT_STAGES
@@ -251,8 +283,37 @@ update_crt_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, in
     if (tid == 0)
         for (; issued < CRT_STAGES; ++issued) issue(issued);
 
-    uint32_t S[2][2][4];
-    uint64_t X[2][2][4];
+    // byte offsets of this thread's fragments inside a stage (the swizzle
+    // uses row & 7 = g for every row and column the thread touches)
+    const int arow = (wm * 32 + g) * CRT_KB + 4 * t4;
+    const int bcol = (wn * 16 + g) * CRT_KB + 4 * t4;
+    int failed = 0;
+    int q_fail = CRT_L;   // first modulus whose data never arrived
+    // waits for modulus q's stage and runs its GEMM into D (false, on every
+    // thread, if the data never arrived)
+    auto gemm_modulus = [&](int q, int (&D)[2][2][4]) -> bool {
+        const int s = q % CRT_STAGES;
+        if (!mbar_wait(bar0 + 8 * s, (uint32_t)((q / CRT_STAGES) & 1), spin)) failed = 1;
+        if (__syncthreads_or(failed)) {
+            failed = 1;
+            q_fail = q;
+            return false;
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) D[a][b][e] = 0;
+        crt_mma_stage(D, smem + s * CRT_STAGE_BYTES, smem + s * CRT_STAGE_BYTES + CRT_A_BYTES, arow, bcol, g,
+                      ksteps);
+        return true;
+    };
+
+    // S = sum_i D'_i floor(2^38 / m_i) and X = sum_i D'_i ((M / m_i) mod p),
+    // exact signed 64-bit sums (|S|, |X| < 9 * 2^21 * 2^31 < 2^56)
+    int64_t S[2][2][4], X[2][2][4];
+    int Dc[2][2][4], Dn[2][2][4];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -262,75 +323,34 @@ update_crt_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, in
                 S[a][b][e] = 0;
                 X[a][b][e] = 0;
             }
-
-    // byte offsets of this thread's fragments inside a stage (the swizzle
-    // uses row & 7 = g for every row and column the thread touches)
-    const int arow = (wm * 32 + g) * CRT_KB + 4 * t4;
-    const int bcol = (wn * 16 + g) * CRT_KB + 4 * t4;
-    bool failed = false;
-    int q = 0;
-
-#pragma unroll 1
-    for (; q < CRT_L; ++q) {
-        const int s = q % CRT_STAGES;
-        if (!mbar_wait(bar0 + 8 * s, (uint32_t)((q / CRT_STAGES) & 1), spin)) failed = true;
-        if (__syncthreads_or(failed)) {
-            failed = true;
-            break;
-        }
-        const uint8_t* As = smem + s * CRT_STAGE_BYTES;
-        const uint8_t* Bs = As + CRT_A_BYTES;
-        int D[2][2][4];
+    gemm_modulus(0, Dc);
+    // software pipeline over the moduli: the GEMM of modulus q + 1 is issued
+    // before the reconstruction step of modulus q, so the tensor pipe works
+    // while the integer pipe folds D'_q into S and X
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) D[a][b][e] = 0;
-#pragma unroll 1
-        for (int ks = 0; ks < ksteps; ++ks) {
-            const int c_lo = ((2 * ks) ^ g) * 16, c_hi = ((2 * ks + 1) ^ g) * 16;
-            uint32_t af[2][4], bf[2][2];
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const uint8_t* p0 = As + arow + a * 16 * CRT_KB;
-                af[a][0] = *reinterpret_cast<const uint32_t*>(p0 + c_lo);
-                af[a][1] = *reinterpret_cast<const uint32_t*>(p0 + 8 * CRT_KB + c_lo);
-                af[a][2] = *reinterpret_cast<const uint32_t*>(p0 + c_hi);
-                af[a][3] = *reinterpret_cast<const uint32_t*>(p0 + 8 * CRT_KB + c_hi);
-            }
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const uint8_t* p0 = Bs + bcol + b * 8 * CRT_KB;
-                bf[b][0] = *reinterpret_cast<const uint32_t*>(p0 + c_lo);
-                bf[b][1] = *reinterpret_cast<const uint32_t*>(p0 + c_hi);
-            }
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) mma_s8(D[a][b], af[a][0], af[a][1], af[a][2], af[a][3], bf[b][0], bf[b][1]);
-        }
-        __syncthreads();   // every warp has read stage s: it may be refilled
+    for (int q = 0; q < CRT_L; ++q) {
+        if (failed) break;
+        if (q + 1 < CRT_L && !gemm_modulus(q + 1, Dn)) break;
+        __syncthreads();   // every warp has read stage q % CRT_STAGES: it may be refilled
         if (tid == 0 && issued < CRT_L) issue(issued++);
-        // step 3 for modulus q
-        const uint32_t mq = cc.m[q], off = cc.off21[q], mgc = cc.mgc[q], w16 = cc.w16[q], wp = cc.wp[q];
+        const int32_t c38 = (int32_t)cc.c38[q], wp = (int32_t)cc.wp[q];
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 2; ++b)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const uint32_t t = small_mod24((uint32_t)D[a][b][e] + off, mq, mgc);
-                    S[a][b][e] += t * w16;
-                    X[a][b][e] += (uint64_t)t * wp;
+                    mac_s64(S[a][b][e], Dc[a][b][e], c38);
+                    mac_s64(X[a][b][e], Dc[a][b][e], wp);
+                    Dc[a][b][e] = Dn[a][b][e];
                 }
     }
     if (failed) {
         // wait (bounded) for the copies still in flight into this block's
-        // buffers (loads q .. issued - 1), then report and leave
+        // buffers (loads q_fail .. issued - 1), then report and leave
         if (tid == 0) {
             atomicCAS(status, 0, (int)LINAC_ERR_TIMEOUT);
-            for (int j = q; j < issued; ++j)
+            for (int j = q_fail; j < issued; ++j)
                 (void)mbar_wait(bar0 + 8 * (j % CRT_STAGES), (uint32_t)((j / CRT_STAGES) & 1), spin);
         }
         __syncthreads();
@@ -370,9 +390,10 @@ update_crt_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, in
 #pragma unroll
                     for (int qq = 0; qq < 2; ++qq) {
                         const int e = hh * 2 + qq;
-                        const uint32_t alpha = (S[a][b][e] + 32768u) >> 16;
-                        const uint64_t x = X[a][b][e] + (uint64_t)alpha * cc.negMp;
-                        out[qq] = submod(cval[qq], reduce64(x, f), f);
+                        // beta = nearest integer to S / 2^38 (floor of S / 2^38 + 1/2)
+                        const int64_t beta = (S[a][b][e] + (1LL << 37)) >> 38;
+                        const int64_t x = X[a][b][e] + beta * (int64_t)cc.negMp;
+                        out[qq] = submod(cval[qq], reduce_signed(x, f), f);
                     }
                 }
                 if (pair) *reinterpret_cast<uint2*>(dst) = make_uint2(out[0], out[1]);
@@ -395,8 +416,8 @@ linac_status launch_update_crt(uint32_t* M, int64_t m, int64_t n, int64_t ld, in
         crt_split_kernel<true><<<(unsigned)((ncols + 63) / 64), 256, 0, stream>>>(R, ldR, ncols, st, cc, crt->Rr,
                                                                                  crt->n_pad);
     }
-    LINAC_CUDA_TRY(cudaFuncSetAttribute(update_crt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)CRT_SMEM));
+    linac_status as = ensure_dynamic_smem((const void*)update_crt_kernel, (int)CRT_SMEM);
+    if (as != LINAC_OK) return as;
     dim3 grid((unsigned)((ncols + CRT_BN - 1) / CRT_BN), (unsigned)((m + CRT_BM - 1) / CRT_BM));
     {
         ProfScope ps(stream, PROF_UPDATE_CRT);

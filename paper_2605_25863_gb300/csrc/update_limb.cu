@@ -254,8 +254,8 @@ linac_status launch_update_limb(uint32_t* M, int64_t m, int64_t n, int64_t ld, i
         limb_split_r_kernel<<<(unsigned)((ncols + 127) / 128 * 2), 256, 0, stream>>>(R, ldR, ncols, st, f,
                                                                                       limb->Rl, limb->n_pad);
     }
-    LINAC_CUDA_TRY(cudaFuncSetAttribute(update_limb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)LIMB_SMEM));
+    linac_status as = ensure_dynamic_smem((const void*)update_limb_kernel, (int)LIMB_SMEM);
+    if (as != LINAC_OK) return as;
     dim3 grid((unsigned)((ncols + LIMB_BN - 1) / LIMB_BN), (unsigned)((m + LIMB_BM - 1) / LIMB_BM));
     {
         ProfScope ps(stream, PROF_UPDATE_LIMB);

@@ -94,6 +94,8 @@ def lib():
         L.linac_solve64.argtypes = [vp, i64, i64, i64, vp, i64, i64, u64, vp, i64, vp, vp, vp, vp]
         L.linac_null_space64.argtypes = [vp, i64, i64, i64, vp, vp, u64, vp, i64, i64, vp, vp, vp]
         L.linac_rank_factor64.argtypes = [vp, i64, i64, i64, vp, vp, vp, i64, i64, vp]
+        L.linac_rref_host.argtypes = [vp, i64, i64, i64, u32, vp, vp, vp]
+        L.linac_rref_host.restype = ctypes.c_int
         L.linac_set_wait_limit.argtypes = [i64]
         L.linac_set_wait_limit.restype = ctypes.c_int
         L.linac_debug_inject_wait_failure.argtypes = [i32]
@@ -171,6 +173,33 @@ def linac_rref(A: torch.Tensor, p: int, *, ncols_search: int | None = None, path
     _check(lib().linac_rref_ex(ptr, m, n, ld, p, ns, rank.data_ptr(), piv.data_ptr(), ctypes.byref(o),
                                _stream_ptr(stream)), "linac_rref")
     return rank, piv[:min(m, ns)]
+
+
+def padded_host(rows: int, cols: int) -> torch.Tensor:
+    """A zeroed rows x cols int32 view of PINNED host memory whose row stride
+    is a multiple of 4 (the layout linac_rref_host takes)."""
+    ld = max(cols + (-cols) % 4, 4)
+    return torch.zeros((rows, ld), dtype=torch.int32, pin_memory=True)[:, :cols]
+
+
+def linac_rref_host(A: torch.Tensor, p: int, *, rank: torch.Tensor | None = None,
+                    pivots: torch.Tensor | None = None, stream=None):
+    """In-place RREF of a matrix in pinned host memory (see padded_host); the
+    transfers happen inside the call.  Returns (rank, pivots) as pinned CPU
+    int32 tensors, valid once the stream has been synchronised."""
+    if not isinstance(A, torch.Tensor) or A.dim() != 2 or A.is_cuda or not A.is_pinned():
+        raise ValueError("A must be a 2-D pinned CPU tensor")
+    if A.dtype not in (torch.int32, torch.uint32) or (A.stride(1) != 1 and A.shape[1] > 1):
+        raise ValueError("A must be row-major int32 or uint32")
+    m, n = A.shape
+    ld = A.stride(0) if m > 1 else max(n + (-n) % 4, 4)
+    if rank is None:
+        rank = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+    if pivots is None:
+        pivots = torch.full((max(min(m, n), 1),), -1, dtype=torch.int32, pin_memory=True)
+    _check(lib().linac_rref_host(A.data_ptr(), m, n, ld, p, rank.data_ptr(), pivots.data_ptr(),
+                                 _stream_ptr(stream)), "linac_rref_host")
+    return rank, pivots[:min(m, n)]
 
 
 def linac_solve(A: torch.Tensor, B: torch.Tensor, p: int, *, path="auto", nb: int = 0,

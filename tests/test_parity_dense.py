@@ -246,3 +246,31 @@ def test_crt_and_plain_agree_on_workload_4096():
     Rc, rc, pc = gpu_rref(M, P31, path="crt")
     Rp, rp, pp = gpu_rref(M, P31, path="plain")
     assert rc == rp == 4032 and np.array_equal(pc, pp) and np.array_equal(Rc, Rp)
+
+
+@pytest.mark.parametrize("path", ["plain", "crt"])
+def test_rref_replays_in_a_cuda_graph(path):
+    """linac_rref is stream-ordered with no host synchronisation: after one
+    uncaptured call (which creates the scratch), the call captures into a
+    CUDA graph; replays on restored input are exact."""
+    M, _ = synth.rank_deficient(m=700, n=660, d=9, p=P31, seed=71)
+    pristine = linac.to_device(M)
+    A = linac.padded(*M.shape)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        A.copy_(pristine)
+        rank, piv = linac.linac_rref(A, P31, path=path, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        A.copy_(pristine)
+        rank, piv = linac.linac_rref(A, P31, path=path, stream=s)
+    R0, r0, piv0, _ = oracle.rref(M, P31, nthreads=NTH)
+    for _ in range(2):
+        A.zero_()
+        with torch.cuda.stream(s):
+            g.replay()
+        s.synchronize()
+        assert int(rank.item()) == r0 == 660
+        assert np.array_equal(piv.cpu().numpy()[:r0], piv0)
+        assert np.array_equal(A.cpu().numpy().view(np.uint32), R0)
