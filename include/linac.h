@@ -175,6 +175,32 @@ linac_status linac_solve_ex(const uint32_t *d_A, int64_t m, int64_t nA, int64_t 
                             int32_t *d_rank, int32_t *d_pivots,
                             const linac_options *opts, cudaStream_t stream);
 
+/*
+ * linac_lup -- LUP factorisation P A = L U over Z/pZ, the option section 6
+ * ("Conclusions and Outlook") names beside the rank decomposition.  The
+ * elimination is the column loop of section 3.2 applied only to the rows not
+ * yet used as pivots, without rescaling; the pivot of each column is the
+ * lowest-index row, in the original order, among those rows with a nonzero
+ * entry there.  This makes P, L and U unique:
+ *   d_A      m x n (ldA), read only.
+ *   d_perm   m int32: row i of P A is row d_perm[i] of A; the pivot rows come
+ *            first in pivot order, then the other rows in increasing order.
+ *   d_L      m x min(m, n) (ldL): the first min(m, n) columns of the m x m
+ *            unit lower triangular factor (L[i][i] = 1; L[i][t] for i > t,
+ *            t < rank is the multiplier row d_perm[i] took for pivot t;
+ *            column t >= rank is the unit vector e_t).  The remaining columns
+ *            of the m x m factor are those of the identity.
+ *   d_U      m x n (ldU): row-echelon form; row t < rank is zero left of
+ *            d_pivots[t] and nonzero there; rows rank..m-1 are zero.
+ *   d_rank, d_pivots  rank and pivot columns (min(m, n) entries, -1 after
+ *            the rank), the same as linac_rref's.
+ * Scratch: about (m + 128) * n * 4 + m * 1.1 KB bytes per stream.  Errors: as
+ * linac_rref; LINAC_ERR_ARG also for ldL < min(m, n) or ldU < n.
+ */
+linac_status linac_lup(const uint32_t *d_A, int64_t m, int64_t n, int64_t ldA, uint32_t p,
+                       uint32_t *d_L, int64_t ldL, uint32_t *d_U, int64_t ldU, int32_t *d_perm,
+                       int32_t *d_rank, int32_t *d_pivots, cudaStream_t stream);
+
 /* Flags for linac_rref_batched. */
 #define LINAC_SHARED_PATTERN 1u  /* all systems share one pivot pattern: find it
                                     with one probe elimination, reuse it, and fall

@@ -361,6 +361,20 @@ linac_status linac_solve(const uint32_t* d_A, int64_t m, int64_t nA, int64_t ldA
                           nullptr, stream);
 }
 
+linac_status linac_lup(const uint32_t* d_A, int64_t m, int64_t n, int64_t ldA, uint32_t p, uint32_t* d_L,
+                       int64_t ldL, uint32_t* d_U, int64_t ldU, int32_t* d_perm, int32_t* d_rank,
+                       int32_t* d_pivots, cudaStream_t stream) {
+    linac_status s = check_matrix(d_A, m, n, ldA);
+    if (s != LINAC_OK) return s;
+    const int64_t mn = std::min(m, n);
+    if (!d_rank || (m > 0 && !d_perm) || (mn > 0 && (!d_pivots || !d_L)) || (m > 0 && n > 0 && !d_U))
+        return LINAC_ERR_ARG;
+    if (ldL < mn || ldU < n) return LINAC_ERR_ARG;
+    if (!prime_ok(p)) return LINAC_ERR_PRIME;
+    if ((s = reset_status(stream)) != LINAC_OK) return s;
+    return lup_factor(d_A, m, n, ldA, make_field(p), d_L, ldL, d_U, ldU, d_perm, d_rank, d_pivots, stream);
+}
+
 linac_status linac_rref_batched(uint32_t* d_data, const int64_t* d_offsets, const int32_t* d_m,
                                 const int32_t* d_n, const int32_t* d_ld, const int32_t* d_nsearch,
                                 int32_t batch, int32_t max_m, int32_t max_n, uint32_t p, uint32_t flags,

@@ -128,7 +128,7 @@ __device__ __forceinline__ int panel_block_min(int v, int* red, int* out) {
 // post slot is reused two columns later, after another cluster barrier.
 __global__ void __cluster_dims__(WIN_CTAS, 1, 1) __launch_bounds__(WIN_THREADS)
 window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f, DenseState* st,
-              uint32_t* __restrict__ panelU, int G) {
+              uint32_t* __restrict__ panelU, int G, const int32_t* __restrict__ rowmap) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     __shared__ __align__(16) uint32_t P[WIN_ROWS_CTA * (NB_MAX + 1)];
@@ -147,7 +147,7 @@ window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int
     const int lrows = max(0, min(WIN_ROWS_CTA, rows - g0));            // rows held here
     for (int e = tid; e < lrows * w; e += WIN_THREADS) {
         const int i = e / w, j = e - i * w;
-        P[i * SW + j] = to_mont(M[(r + g0 + i) * ld + c0 + j], f);
+        P[i * SW + j] = to_mont(M[map_row(rowmap, r, g0 + i) * ld + c0 + j], f);
     }
     for (int i = tid; i < WIN_ROWS_CTA; i += WIN_THREADS) isp[i] = 0;
     __syncthreads();
@@ -208,7 +208,7 @@ window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int
         for (int t = tid; t < kk; t += WIN_THREADS) {
             const int q = own[t];
             if (q / WIN_ROWS_CTA != c) continue;
-            st->Pi[t] = (int32_t)(r + q);
+            st->Pi[t] = (int32_t)map_row(rowmap, r, q);
         }
         for (int e = tid; e < kk * w; e += WIN_THREADS) {
             const int t = e / w, j = e - t * w;
@@ -232,7 +232,8 @@ window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int
 
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, int S_max,
-             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status, WaitLimit wl) {
+             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status, WaitLimit wl,
+             const int32_t* __restrict__ rowmap) {
     extern __shared__ __align__(16) uint32_t sm[];
     const int SW = w + 1;
     uint32_t* P = sm;
@@ -249,9 +250,9 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
     const int64_t r = st->r;
     const int64_t left = m - r;
     const int S = left > 0 ? (int)((left + G - 1) / G) : 0;
-    const int64_t lo = r + (int64_t)b * S;
+    const int64_t lo = (int64_t)b * S;   // first position of this block's slab
     int nrows = 0;
-    if (S > 0 && lo < m) nrows = (int)min((int64_t)S, m - lo);
+    if (S > 0 && lo < left) nrows = (int)min((int64_t)S, left - lo);
 
     // the slab, the published candidate rows and prow hold Montgomery forms
     // x R mod p (R = 2^32): each fraction-free update is two products and one
@@ -259,7 +260,7 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
     // they are written to panelU
     for (int64_t e = tid; e < (int64_t)nrows * w; e += blockDim.x) {
         const int i = (int)(e / w), j = (int)(e % w);
-        P[i * SW + j] = to_mont(M[(lo + i) * ld + c0 + j], f);
+        P[i * SW + j] = to_mont(M[map_row(rowmap, r, lo + i) * ld + c0 + j], f);
     }
     for (int i = tid; i < nrows; i += blockDim.x) isp[i] = 0;
     for (int t = tid; t < NB_MAX; t += blockDim.x) own[t] = -1;
@@ -313,12 +314,12 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
         __syncthreads();
         const int q = s_q;
         if (q != INT_MAX) {
-            const int owner = (int)((q - r) / S);
+            const int owner = q / S;
             const uint32_t* src = cand + ((size_t)par * G + owner) * NB_MAX;
             for (int j = tid; j < w; j += blockDim.x) prow[j] = __ldcg(src + j);
             if (tid == 0) {
                 if (b == owner) { isp[q - lo] = 1; own[kk] = (int)(q - lo); }
-                if (b == 0) { st->Pi[kk] = q; st->J[kk] = c0 + col; }
+                if (b == 0) { st->Pi[kk] = (int32_t)map_row(rowmap, r, q); st->J[kk] = c0 + col; }
             }
             ++kk;
             __syncthreads();
@@ -391,18 +392,22 @@ panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int 
 // transposed multipliers with coalesced stores.
 __global__ void __launch_bounds__(256)
 gather_f_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f,
-                const DenseState* __restrict__ st, int32_t* __restrict__ Ft, int64_t ldF) {
+                const DenseState* __restrict__ st, int32_t* __restrict__ Ft, int64_t ldF,
+                const int32_t* __restrict__ rowmap) {
     __shared__ uint32_t seg[64][NB_MAX + 1];
     __shared__ int Jl[NB_MAX];
     const int k = st->k;
     if (k == 0) return;
     const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
     const int64_t row0 = (int64_t)blockIdx.x * 64;
+    // with a row map, the rows are those left after this panel's pivots
+    if (rowmap) m = min(m, (int64_t)(m - st->r - k));
+    if (row0 >= m) return;
     for (int t = threadIdx.x; t < k; t += blockDim.x) Jl[t] = st->J[t] - c0;
     for (int e = threadIdx.x; e < 64 * w; e += blockDim.x) {
         const int i = e / w, j = e % w;
         const int64_t row = row0 + i;
-        seg[i][j] = row < m ? M[row * ld + c0 + j] : 0u;
+        seg[i][j] = row < m ? M[map_row(rowmap, 0, row) * ld + c0 + j] : 0u;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < kpad * 64; e += blockDim.x) {
@@ -644,6 +649,8 @@ DenseLayout dense_layout(int64_t m, int64_t n, int G) {
     return L;
 }
 
+}  // namespace
+
 int panel_grid(int64_t m) {
     const int nsm = sm_count();
     int64_t g = (m + 127) / 128;
@@ -653,8 +660,6 @@ int panel_grid(int64_t m) {
 size_t panel_smem(int S_max, int w) {
     return (size_t)S_max * (w + 1) * 4 + NB_MAX * 4 + NB_MAX * 4 + (size_t)S_max + 16;
 }
-
-}  // namespace
 
 int dense_default_nb(int64_t m, int64_t n) {
     (void)n;
@@ -742,7 +747,7 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
         const int64_t ncols = n - c0;
         {
             ProfScope ps(stream, PROF_PANEL);
-            window_kernel<<<WIN_CTAS, WIN_THREADS, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, panelU, G);
+            window_kernel<<<WIN_CTAS, WIN_THREADS, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, panelU, G, nullptr);
         }
         {
             const uint32_t* Mc = dA;
@@ -750,14 +755,16 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
             int c0_ = (int)c0, w_ = w, S_ = S_max;
             Field f_ = f;
             WaitLimit wl = wait_limit();
-            void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status, &wl};
+            const int32_t* rowmap = nullptr;
+            void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status, &wl, &rowmap};
             ProfScope ps(stream, PROF_PANEL);
             LINAC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_kernel, dim3(G), dim3(PANEL_THREADS),
                                                        args, psmem, stream));
         }
         {
             ProfScope ps(stream, PROF_GATHER_F);
-            gather_f_kernel<<<(unsigned)((m + 63) / 64), 256, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, Ft, L.ldF);
+            gather_f_kernel<<<(unsigned)((m + 63) / 64), 256, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, Ft, L.ldF,
+                                                                           nullptr);
         }
         {
             const unsigned gx = (unsigned)std::min<int64_t>((ncols + 1023) / 1024, 64);

@@ -15,17 +15,34 @@ constexpr int WIN_ROWS_CTA = (NB_MAX + WIN_EXTRA + WIN_CTAS - 1) / WIN_CTAS;   /
 constexpr int EINV_COLS = 8;         // columns of E = G^{-1} per einv_kernel block
 constexpr size_t EINV_SMEM = ((size_t)NB_MAX * (NB_MAX + 1) + (size_t)NB_MAX * EINV_COLS) * 4;
 
+// Row maps.  The pivot search and the multiplier gather address the
+// remaining rows by their position x in [0, m - r): the row is r + x when
+// rowmap is null (the RREF keeps the remaining rows contiguous), rowmap[x]
+// otherwise (the LUP factorisation keeps them in their original places and
+// lists them in increasing order, so the lowest position is the lowest
+// original row).  The gather addresses all rows the same way, with x from 0.
+__device__ __forceinline__ int64_t map_row(const int32_t* rowmap, int64_t base, int64_t x) {
+    return rowmap ? (int64_t)rowmap[x] : base + x;
+}
+
+// Blocks of the cooperative panel search for m rows, and its dynamic shared
+// memory for slabs of S_max rows and panel width w.
+int panel_grid(int64_t m);
+size_t panel_smem(int S_max, int w);
+
 __global__ void init_kernel(DenseState* st, int32_t* d_pivots, int64_t npiv, int32_t* d_rank);
 __global__ void finish_kernel(DenseState* st, int32_t* d_pivots, int32_t* d_rank);
 __global__ void __cluster_dims__(WIN_CTAS, 1, 1) __launch_bounds__(WIN_THREADS)
 window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f, DenseState* st,
-              uint32_t* __restrict__ panelU, int G);
+              uint32_t* __restrict__ panelU, int G, const int32_t* __restrict__ rowmap);
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, int S_max,
-             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status, WaitLimit wl);
+             Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status, WaitLimit wl,
+             const int32_t* __restrict__ rowmap);
 __global__ void __launch_bounds__(256)
 gather_f_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f,
-                const DenseState* __restrict__ st, int32_t* __restrict__ Ft, int64_t ldF);
+                const DenseState* __restrict__ st, int32_t* __restrict__ Ft, int64_t ldF,
+                const int32_t* __restrict__ rowmap);
 __global__ void gather_w_kernel(const uint32_t* __restrict__ M, int64_t ld, int64_t ncols, int c0, Field f,
                                 const DenseState* __restrict__ st, int32_t* __restrict__ W, int64_t ldW);
 __global__ void heads_inverse_kernel(DenseState* st, const uint32_t* __restrict__ panelU, int c0,

@@ -34,7 +34,7 @@ linac_status scratch_get(cudaStream_t stream, size_t bytes, void** ptr);
 // augmented matrix, 2 = batched driver, 3 = limb planes, 4 = null-space
 // column positions, 6 = uint64 elimination, 7 = the uint64 solve's
 // augmented matrix, 8 = residue planes of the multi-modular update, 9 = the
-// device copy of linac_rref_host's matrix).
+// device copy of linac_rref_host's matrix, 10 = the LUP factorisation).
 linac_status scratch_get_slot(cudaStream_t stream, int slot, size_t bytes, void** ptr);
 
 // Device status word of the most recent call on this (device, stream): lives
@@ -76,6 +76,11 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
                         int path, int nb, cudaStream_t stream);
 size_t dense_workspace_bytes(int64_t m, int64_t n, int nb);
 int dense_default_nb(int64_t m, int64_t n);
+
+// LUP factorisation P A = L U (lup.cu): L is m x min(m, n), U is m x n.
+linac_status lup_factor(const uint32_t* dA, int64_t m, int64_t n, int64_t ldA, const Field& f, uint32_t* dL,
+                        int64_t ldL, uint32_t* dU, int64_t ldU, int32_t* d_perm, int32_t* d_rank,
+                        int32_t* d_pivots, cudaStream_t stream);
 
 // Solve helpers (dense.cu).
 linac_status solve_pack(const uint32_t* dA, int64_t m, int64_t nA, int64_t ldA,

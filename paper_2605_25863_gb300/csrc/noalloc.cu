@@ -158,18 +158,20 @@ extern "C" linac_status linac_rref_noalloc(uint32_t* d_A, int64_t m, int64_t n, 
     for (int64_t c0 = 0; c0 < n; c0 += nb) {
         const int w = (int)std::min<int64_t>(nb, n - c0);
         const int64_t ncols = n - c0;
-        window_kernel<<<WIN_CTAS, WIN_THREADS, 0, stream>>>(d_A, m, ld, (int)c0, w, f, st, panelU, G);
+        window_kernel<<<WIN_CTAS, WIN_THREADS, 0, stream>>>(d_A, m, ld, (int)c0, w, f, st, panelU, G, nullptr);
         {
             const uint32_t* Mc = d_A;
             int64_t m_ = m, ld_ = ld;
             int c0_ = (int)c0, w_ = w, S_ = S_max;
             Field f_ = f;
             WaitLimit wl = wl0;
-            void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status, &wl};
+            const int32_t* rowmap = nullptr;
+            void* args[] = {(void*)&Mc, &m_, &ld_, &c0_, &w_, &S_, &f_, &st, &cand, &panelU, &status, &wl, &rowmap};
             LINAC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_kernel, dim3(G), dim3(PANEL_THREADS),
                                                        args, psmem, stream));
         }
-        gather_f_kernel<<<(unsigned)((m + 63) / 64), 256, 0, stream>>>(d_A, m, ld, (int)c0, w, f, st, Ft, L.ldF);
+        gather_f_kernel<<<(unsigned)((m + 63) / 64), 256, 0, stream>>>(d_A, m, ld, (int)c0, w, f, st, Ft, L.ldF,
+                                                                       nullptr);
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncols + 1023) / 1024, 64));
         gather_w_kernel<<<dim3(gx, NB_MAX), 256, 0, stream>>>(d_A, ld, ncols, (int)c0, f, st, W, L.ldW);
         heads_inverse_kernel<<<1, NB_MAX, 0, stream>>>(st, panelU, (int)c0, f.p, status);

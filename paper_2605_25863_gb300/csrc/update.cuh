@@ -52,6 +52,13 @@ linac_status launch_update(int path, uint32_t* M, int64_t m, int64_t n, int64_t 
                            const int32_t* R, int64_t ldR, const LimbScratch* limb,
                            const CrtScratch* crt, int* status, cudaStream_t stream);
 
+// M[rowmap[i], c0:n] <- M[rowmap[i], c0:n] - F[i] R for i < mrows (the LUP
+// factorisation's trailing update of the rows that are not pivots yet; Ft is
+// k x ldF with column i holding row rowmap[i]'s multipliers).
+linac_status launch_update_rows(uint32_t* M, int64_t mrows, int64_t n, int64_t ld, int c0, const Field& f,
+                                const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,
+                                int64_t ldR, const int32_t* rowmap, cudaStream_t stream);
+
 // R[t][j] <- balanced(sum_s E[t][s] W[s][j]) for t < kpad(k), j < ncols, with
 // Et = E transposed (kpad x ldE) and W (kpad x ldW), both balanced int32.
 linac_status launch_gemm_assign(const Field& f, const DenseState* st, const int32_t* Et, int64_t ldE,

@@ -21,7 +21,9 @@ namespace linac {
 
 // MODE 0: trailing update of M (rows [r, r+k) receive R).  MODE 1: plain
 // product written as balanced residues to Out (k_pad x ldOut); M, m, c0 unused
-// except that m bounds the A rows read.
+// except that m bounds the A rows read.  MODE 2: trailing update of the rows
+// rowmap[0..m) of M (the rows of the LUP factorisation that are not pivots
+// yet); A row i is the multiplier row of M's row rowmap[i].
 //
 // Tiling: 128 x 64 outputs per 256-thread block, 8 x 4 per thread (two 4-row
 // groups, one 4-column group), 128 registers so two blocks share an SM; K in
@@ -33,7 +35,7 @@ __global__ void __launch_bounds__(256, 2)
 update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, int c0, Field f,
                     FoldShifts fs, const DenseState* __restrict__ st, const int32_t* __restrict__ Ft,
                     int64_t ldF, const int32_t* __restrict__ R, int64_t ldR, int32_t* __restrict__ Out,
-                    int64_t ldOut) {
+                    int64_t ldOut, const int32_t* __restrict__ rowmap) {
     static_assert(UPD_BK % FOLD == 0, "fold cadence must divide the K chunk");
     __shared__ __align__(16) int32_t As[2][UPD_BK][UPD_BM];
     __shared__ __align__(16) int32_t Bs[2][UPD_BK][UPD_BN2];
@@ -42,6 +44,10 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
     const int r = st->r;
     const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
     const int64_t row0 = (int64_t)blockIdx.y * UPD_BM;
+    if (MODE == 2) {   // the rows left after this panel's pivots
+        m = min(m, (int64_t)(m - r - k));
+        if (row0 >= m) return;
+    }
     const int64_t col0 = (int64_t)blockIdx.x * UPD_BN2;   // relative to c0
     const int64_t ncols = n - c0;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -120,10 +126,10 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
     for (int i = 0; i < 8; ++i) {
         const int64_t row = row0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
         if (row >= m) continue;
-        const bool pivot_row = row >= r && row < r + k;
+        const bool pivot_row = MODE == 0 && row >= r && row < r + k;
         const int64_t col = col0 + tx * 4;
         if (col >= ncols) continue;
-        uint32_t* dst = M + row * ld + c0 + col;
+        uint32_t* dst = M + (MODE == 2 ? (int64_t)rowmap[row] : row) * ld + c0 + col;
         uint32_t out[4];
         if (pivot_row) {
             const int32_t* rr = R + (int64_t)(row - r) * ldR + col;
@@ -151,12 +157,13 @@ namespace {
 template <int MODE>
 void launch_plain(dim3 grid, cudaStream_t stream, uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0,
                   const Field& f, const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,
-                  int64_t ldR, int32_t* Out, int64_t ldOut) {
+                  int64_t ldR, int32_t* Out, int64_t ldOut, const int32_t* rowmap = nullptr) {
     FoldShifts fs;
     const int sh = fold_shifts(f, &fs);
     const int fold = f.fold >= 16 ? 16 : (f.fold >= 8 ? 8 : 4);
 #define LINAC_UPD(FO, SH) \
-    update_plain_kernel<FO, SH, MODE><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, fs, st, Ft, ldF, R, ldR, Out, ldOut)
+    update_plain_kernel<FO, SH, MODE><<<grid, 256, 0, stream>>>(M, m, n, ld, c0, f, fs, st, Ft, ldF, R, ldR, Out, ldOut, \
+                                                                 rowmap)
 #define LINAC_UPD_SH(FO)                    \
     switch (sh) {                           \
         case 1: LINAC_UPD(FO, 1); break;    \
@@ -171,6 +178,19 @@ void launch_plain(dim3 grid, cudaStream_t stream, uint32_t* M, int64_t m, int64_
 #undef LINAC_UPD
 }
 }  // namespace
+
+linac_status launch_update_rows(uint32_t* M, int64_t mrows, int64_t n, int64_t ld, int c0, const Field& f,
+                                const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,
+                                int64_t ldR, const int32_t* rowmap, cudaStream_t stream) {
+    const int64_t ncols = n - c0;
+    if (ncols <= 0 || mrows <= 0) return LINAC_OK;
+    if ((mrows + UPD_BM - 1) / UPD_BM > 65535) return LINAC_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)((ncols + UPD_BN2 - 1) / UPD_BN2), (unsigned)((mrows + UPD_BM - 1) / UPD_BM));
+    ProfScope ps(stream, PROF_UPDATE_PLAIN);
+    launch_plain<2>(grid, stream, M, mrows, n, ld, c0, f, st, Ft, ldF, R, ldR, nullptr, 0, rowmap);
+    LINAC_CUDA_TRY(cudaGetLastError());
+    return LINAC_OK;
+}
 
 linac_status launch_update_limb(uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0, const Field& f,
                                 const DenseState* st, const int32_t* Ft, int64_t ldF, const int32_t* R,

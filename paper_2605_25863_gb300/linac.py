@@ -94,6 +94,8 @@ def lib():
         L.linac_solve64.argtypes = [vp, i64, i64, i64, vp, i64, i64, u64, vp, i64, vp, vp, vp, vp]
         L.linac_null_space64.argtypes = [vp, i64, i64, i64, vp, vp, u64, vp, i64, i64, vp, vp, vp]
         L.linac_rank_factor64.argtypes = [vp, i64, i64, i64, vp, vp, vp, i64, i64, vp]
+        L.linac_lup.argtypes = [vp, i64, i64, i64, u32, vp, i64, vp, i64, vp, vp, vp, vp]
+        L.linac_lup.restype = ctypes.c_int
         L.linac_rref_host.argtypes = [vp, i64, i64, i64, u32, vp, vp, vp]
         L.linac_rref_host.restype = ctypes.c_int
         L.linac_set_wait_limit.argtypes = [i64]
@@ -173,6 +175,24 @@ def linac_rref(A: torch.Tensor, p: int, *, ncols_search: int | None = None, path
     _check(lib().linac_rref_ex(ptr, m, n, ld, p, ns, rank.data_ptr(), piv.data_ptr(), ctypes.byref(o),
                                _stream_ptr(stream)), "linac_rref")
     return rank, piv[:min(m, ns)]
+
+
+def linac_lup(A: torch.Tensor, p: int, *, stream=None):
+    """LUP factorisation P A = L U (see include/linac.h).  A is not modified.
+    Returns (L, U, perm, rank, pivots) as CUDA tensors: L m x min(m, n), U
+    m x n, perm m int32 (row i of P A is row perm[i] of A)."""
+    pa, m, n, ld = _matrix(A, "A")
+    mn = min(m, n)
+    Lm = padded(max(m, 1), max(mn, 1), A.device)[:m, :mn]
+    U = padded(max(m, 1), max(n, 1), A.device)[:m, :n]
+    perm = torch.zeros(max(m, 1), dtype=torch.int32, device=A.device)
+    rank = torch.zeros(1, dtype=torch.int32, device=A.device)
+    piv = torch.full((max(mn, 1),), -1, dtype=torch.int32, device=A.device)
+    ldl = max(Lm.stride(0), mn, 1) if m else max(mn, 1)
+    ldu = max(U.stride(0), n, 1) if m else max(n, 1)
+    _check(lib().linac_lup(pa, m, n, ld, p, Lm.data_ptr(), ldl, U.data_ptr(), ldu, perm.data_ptr(),
+                           rank.data_ptr(), piv.data_ptr(), _stream_ptr(stream)), "linac_lup")
+    return Lm, U, perm[:m], rank, piv[:mn]
 
 
 def padded_host(rows: int, cols: int) -> torch.Tensor:

@@ -8,10 +8,15 @@ the result is checked through properties that hold at any size:
   F_p is invertible with probability > 1 - 1/p);
 * the left block of the RREF is exactly the identity (section 5.2:
   [A | B] reduces to [I | X]);
-* A X = B (mod p), checked by Freivalds' test with three random vectors v:
-  A (X v) = B v.  A wrong X passes one trial with probability <= 1/p.  The
-  products are exact integer arithmetic on the CPU (numpy int64 with a
-  16-bit split), independent of the CUDA path.
+* A X = B (mod p) for all 256 right-hand sides, exactly: the product A X
+  (2.7e14 multiply-adds) runs on linac_matmul, the library's exact mod-p
+  product (its own kernel, pinned against the oracle in
+  test_parity_derived.py), and is compared with B entry by entry.  Because A
+  is invertible, X is then the unique solution and the RREF [I | X] is
+  determined, so the check is deterministic;
+* the same identity by Freivalds' test with three random vectors v,
+  A (X v) = B v, in exact integer arithmetic on the CPU (numpy int64 with a
+  16-bit split), independent of the CUDA code.
 """
 import numpy as np
 import pytest
@@ -57,6 +62,12 @@ def test_dense_32768_bench_configuration():
         ref[torch.arange(blk.shape[0], device=dev), torch.arange(r0, r0 + blk.shape[0], device=dev)] = 1
         eye_ok &= bool(torch.equal(blk, ref))
     assert eye_ok, "left block is not the identity"
+    # exact A X = B on the device (A kept in its original state on the host)
+    A0 = torch.from_numpy(orig.view(np.int32)).to(dev)
+    AX = linac.linac_matmul(A0[:, :M_ROWS], A[:, M_ROWS:], P)
+    torch.cuda.synchronize()
+    assert torch.equal(AX, A0[:, M_ROWS:]), "A X != B (mod p) on the device product"
+    del A0, AX
     X = A[:, M_ROWS:].cpu().numpy().view(np.uint32)
     V = np.random.default_rng(2026).integers(0, P, size=(RHS, 3), dtype=np.int64)
     XV = matmul_mod(X, V, P)
