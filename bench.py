@@ -53,11 +53,11 @@ P31 = 2**31 - 1
 IMAD_WIDE_PER_SM_CLK = 32
 # DRAM bytes per output of update_plain_kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of the third panel of the
-# 8192 x 8448 elimination: 480.8 MB for 8192 x 8192 outputs; summary in
+# 8192 x 8448 elimination: 477.8 MB for 8192 x 8192 outputs; summary in
 # profiles/update_plain_rref_8192x8448.md), valid while the kernel's sources
 # hash to UPDATE_SRC_SHA; the traffic is reported as null otherwise
-UPDATE_BYTES_PER_OUTPUT = 480.8e6 / (8192 * 8192)
-UPDATE_SRC_SHA = "b220f7406c7ca3e3"
+UPDATE_BYTES_PER_OUTPUT = 477.8e6 / (8192 * 8192)
+UPDATE_SRC_SHA = "a7542ca4c7ff9976"
 UPDATE_SRC = ["paper_2605_25863_gb300/csrc/update_plain.cu", "paper_2605_25863_gb300/csrc/linac_device.cuh",
               "paper_2605_25863_gb300/csrc/update.cuh"]
 
@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--m", type=int, default=32768, help="rows (= unknowns) of the dense system")
     ap.add_argument("--rhs", type=int, default=256, help="right-hand-side columns")
     ap.add_argument("--nb", type=int, default=128, help="panel width")
-    ap.add_argument("--path", default="auto", choices=["auto", "plain", "limb"])
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "limb", "crt"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU oracle, path comparison and batched legs")
@@ -371,7 +371,7 @@ def run_ours(args):
     value, tot_ms = replica_rate(sum(step_ms), work_macs * args.steps, world, dev)
 
     # dominant kernel: the trailing update
-    upd_name = "update_limb" if args.path == "limb" else "update_plain"
+    upd_name = PATH_KERNEL.get(args.path, "update_plain")
     upd_launches, upd_ms = prof.get(upd_name, (0, 0.0))
     upd_macs = update_work(m, n, piv, nb) * args.steps
     fold = fold_of(p)
@@ -387,6 +387,25 @@ def run_ours(args):
     peaks = {"plain": peak, "plain_basis": f"{sms} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x "
                                            f"{sm_max_mhz:.0f} MHz / {imad_per_mac:.3f} per field MAC",
              "imma_s8": s8_peak, "imma_u8": u8_peak}
+    if upd_name == "update_plain":
+        roof = {"kernel": upd_name, "bound": "alu", "achieved": achieved / 1e12,
+                "peak": peak / 1e12, "unit": "Tfield-MAC/s", "frac": achieved / peak if peak else None,
+                "traffic": traffic,
+                "traffic_basis": "ncu DRAM bytes per output of the 8192 x 8448 capture x outputs per launch"
+                                 if traffic is not None else "kernel changed since the ncu capture",
+                "peak_basis": f"{sms} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x {sm_max_mhz:.0f} MHz"
+                              f" ({clk_src})"
+                              f" / {imad_per_mac:.3f} per field MAC"
+                              f" ({'folds on the ALU pipe' if shift_fold else f'fold every {fold} on the multiply pipe'})",
+                "avg_launch_ms": upd_ms / max(1, upd_launches), "launches": upd_launches}
+    else:   # integer tensor pipe: narrow products per second against the measured mma.sync rate
+        narrow = PATH_NARROW[args.path]
+        tpeak = u8_peak if args.path == "limb" else s8_peak
+        roof = {"kernel": upd_name, "bound": "tensor", "achieved": achieved * narrow / 1e12,
+                "peak": tpeak / 1e12, "unit": "T narrow-MAC/s", "frac": achieved * narrow / tpeak,
+                "traffic": None, "traffic_basis": "not captured for this path",
+                "peak_basis": "measured mma.sync m16n8k32 rate (probes/int_rates.cu)",
+                "avg_launch_ms": upd_ms / max(1, upd_launches), "launches": upd_launches}
     kernel_times = {k: {"launches": v[0], "total_ms": round(v[1], 3),
                         "share": round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4)}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -399,16 +418,7 @@ def run_ours(args):
                    "path": args.path, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "input 4.3 GB > L2, restored by a full device copy before every step"
                          if m == 32768 else "input restored by a full device copy before every step"},
-        "roofline": {"kernel": upd_name, "bound": "alu", "achieved": achieved / 1e12,
-                     "peak": peak / 1e12, "unit": "Tfield-MAC/s", "frac": achieved / peak if peak else None,
-                     "traffic": traffic,
-                     "traffic_basis": "ncu DRAM bytes per output of the 8192 x 8448 capture x outputs per launch"
-                                      if traffic is not None else "kernel changed since the ncu capture",
-                     "peak_basis": f"{sms} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x {sm_max_mhz:.0f} MHz"
-                                   f" ({clk_src})"
-                                   f" / {imad_per_mac:.3f} per field MAC"
-                                   f" ({'folds on the ALU pipe' if shift_fold else f'fold every {fold} on the multiply pipe'})",
-                     "avg_launch_ms": upd_ms / max(1, upd_launches), "launches": upd_launches},
+        "roofline": roof,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "correct": bool(ok),
