@@ -64,9 +64,11 @@ typedef enum {
     LINAC_PATH_AUTO = 0,   /* fastest measured path on this device */
     LINAC_PATH_PLAIN = 1,  /* CUDA cores: lazy signed 64-bit accumulation */
     LINAC_PATH_LIMB = 2,   /* integer tensor pipe: four u8 limbs per residue */
-    LINAC_PATH_CRT = 3     /* integer tensor pipe: residues modulo nine small
+    LINAC_PATH_CRT = 3,    /* integer tensor pipe: residues modulo nine small
                               moduli (s8), exact Chinese-remainder
                               reconstruction of each output */
+    LINAC_PATH_HYBRID = 4  /* both at once: CUDA-core and multi-modular tiles
+                              on different warps of one block per SM */
 } linac_path;
 
 typedef struct {

@@ -279,7 +279,7 @@ linac_status check_matrix64(const void* d, int64_t m, int64_t n, int64_t ld) {
 
 linac_status check_opts(const linac_options* o) {
     if (!o) return LINAC_OK;
-    if (o->path < LINAC_PATH_AUTO || o->path > LINAC_PATH_CRT) return LINAC_ERR_ARG;
+    if (o->path < LINAC_PATH_AUTO || o->path > LINAC_PATH_HYBRID) return LINAC_ERR_ARG;
     if (o->nb < 0 || o->nb > NB_MAX || (o->nb % UPD_BK) != 0) return LINAC_ERR_ARG;
     return LINAC_OK;
 }

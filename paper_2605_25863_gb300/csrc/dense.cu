@@ -727,7 +727,7 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
     }
     CrtScratch crt{};
     bool crt_ok = false;
-    if (path == LINAC_PATH_CRT) {
+    if (path == LINAC_PATH_CRT || path == LINAC_PATH_HYBRID) {
         void* cb = nullptr;
         st_ = scratch_get_slot(stream, 8, crt_scratch_bytes(m, n), &cb);
         if (st_ != LINAC_OK) return st_;
@@ -789,7 +789,8 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
             move_kernel<<<NB_MAX, 256, 0, stream>>>(dA, ld, n, (int)c0, st, Ft, L.ldF);
         }
         linac_status us = launch_update(path, dA, m, n, ld, (int)c0, f, st, Ft, L.ldF, R, L.ldW,
-                                       limb_ok ? &limb : nullptr, crt_ok ? &crt : nullptr, status, stream);
+                                       limb_ok ? &limb : nullptr, crt_ok ? &crt : nullptr, status, &st->next_area,
+                                       stream);
         if (us != LINAC_OK) return us;
         {
             ProfScope ps(stream, PROF_FINISH);

@@ -180,7 +180,7 @@ extern "C" linac_status linac_rref_noalloc(uint32_t* d_A, int64_t m, int64_t n, 
         if (s != LINAC_OK) return s;
         move_kernel<<<NB_MAX, 256, 0, stream>>>(d_A, ld, n, (int)c0, st, Ft, L.ldF);
         s = launch_update(LINAC_PATH_PLAIN, d_A, m, n, ld, (int)c0, f, st, Ft, L.ldF, R, L.ldW, nullptr, nullptr,
-                         status, stream);
+                         status, nullptr, stream);
         if (s != LINAC_OK) return s;
         finish_kernel<<<1, NB_MAX, 0, stream>>>(st, d_pivots, d_rank);
         LINAC_CUDA_TRY(cudaGetLastError());

@@ -25,7 +25,7 @@ const char* g_names[PROF_NCLASSES] = {"init", "panel", "gather_f", "gather_w", "
                                       "update_plain", "update_limb", "limb_split", "finish", "batched",
                                       "solve_pack", "solve_extract", "validate", "pattern", "matmul",
                                       "load_matrix", "derived", "u64_panel", "u64_update",
-                                      "update_crt", "crt_split", "host_copy", "lup"};
+                                      "update_crt", "crt_split", "host_copy", "lup", "update_hybrid"};
 
 cudaEvent_t take_event() {
     if (!g_pool.empty()) {

@@ -11,7 +11,7 @@ enum ProfClass {
     PROF_INIT = 0, PROF_PANEL, PROF_GATHER_F, PROF_GATHER_W, PROF_INVERSE, PROF_TRSM, PROF_MOVE,
     PROF_UPDATE_PLAIN, PROF_UPDATE_LIMB, PROF_LIMB_SPLIT, PROF_FINISH, PROF_BATCHED, PROF_SOLVE_PACK,
     PROF_SOLVE_EXTRACT, PROF_VALIDATE, PROF_PATTERN, PROF_MATMUL, PROF_LOAD_MATRIX, PROF_DERIVED, PROF_U64_PANEL, PROF_U64_UPDATE,
-    PROF_UPDATE_CRT, PROF_CRT_SPLIT, PROF_HOST_COPY, PROF_LUP, PROF_NCLASSES
+    PROF_UPDATE_CRT, PROF_CRT_SPLIT, PROF_HOST_COPY, PROF_LUP, PROF_UPDATE_HYBRID, PROF_NCLASSES
 };
 
 const char* prof_name(int cls);

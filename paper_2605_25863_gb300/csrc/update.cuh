@@ -25,6 +25,8 @@ struct DenseState {
     int32_t Pi[NB_MAX];     // pivot rows of the current panel (absolute, before the move)
     int32_t best[NB_MAX];   // per panel column: lowest candidate row (INT_MAX = none)
     uint32_t hinv[NB_MAX];  // inverses of the pivot heads
+    uint32_t next_area;     // work counter of the hybrid update
+    uint32_t pad2[3];
 };
 
 // Extra scratch used by the limb path (u8 limb planes of F and R).
@@ -50,7 +52,7 @@ void crt_scratch_layout(void* base, int64_t m, int64_t n, CrtScratch* out);
 linac_status launch_update(int path, uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0,
                            const Field& f, const DenseState* st, const int32_t* Ft, int64_t ldF,
                            const int32_t* R, int64_t ldR, const LimbScratch* limb,
-                           const CrtScratch* crt, int* status, cudaStream_t stream);
+                           const CrtScratch* crt, int* status, unsigned int* counter, cudaStream_t stream);
 
 // M[rowmap[i], c0:n] <- M[rowmap[i], c0:n] - F[i] R for i < mrows (the LUP
 // factorisation's trailing update of the rows that are not pivots yet; Ft is

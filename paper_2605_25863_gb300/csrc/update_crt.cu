@@ -45,35 +45,14 @@
 #include "linac_host.h"
 #include "profile.h"
 #include "update.cuh"
+#include "update_tiles.cuh"
 
 namespace linac {
 
 namespace {
-
-constexpr int CRT_L = 9;
 constexpr uint32_t CRT_MODULI[CRT_L] = {256, 255, 253, 251, 247, 241, 239, 233, 229};
-constexpr int CRT_BM = 64, CRT_BN = 64;
-constexpr int CRT_KB = NB_MAX;                      // bytes per residue row (k <= 128)
 constexpr int CRT_THREADS = 256;
-constexpr int CRT_STAGES = 3;
-constexpr int CRT_A_BYTES = CRT_BM * CRT_KB;        // 8 KB
-constexpr int CRT_B_BYTES = CRT_BN * CRT_KB;        // 8 KB
-constexpr int CRT_STAGE_BYTES = CRT_A_BYTES + CRT_B_BYTES;
-constexpr size_t CRT_SMEM = (size_t)CRT_STAGES * CRT_STAGE_BYTES + 64;
-
 }  // namespace
-
-// Per-prime constants of the reconstruction (computed on the host).
-struct CrtConsts {
-    uint32_t m[CRT_L];      // the moduli
-    uint32_t y[CRT_L];      // (M / m_i)^(-1) mod m_i
-    uint32_t off30[CRT_L];  // m_i ceil(2^30 / m_i): makes a balanced residue of p non-negative
-    uint32_t mgf[CRT_L];    // floor(2^32 / m_i)
-    uint32_t mgc[CRT_L];    // ceil(2^32 / m_i)
-    uint32_t c38[CRT_L];    // floor(2^38 / m_i) (below 2^31)
-    uint32_t wp[CRT_L];     // (M / m_i) mod p
-    uint32_t negMp;         // (-M) mod p
-};
 
 CrtConsts make_crt(uint32_t p) {
     CrtConsts c{};
@@ -170,82 +149,8 @@ crt_split_kernel(const int32_t* __restrict__ T, int64_t ldT, int64_t nx, const D
 }
 
 // ---------------------------------------------------------------------------
-// The tensor-core update
-
-__device__ __forceinline__ void mma_s8(int (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                       uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done;
-}
-
-// Wait for phase `parity` of an mbarrier, giving up (false) after about
-// `limit` SM clock cycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (clock64() - t0 < limit)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-// The residue GEMM of one modulus for this thread's 2 x 2 fragments (32 x 16
-// outputs per warp): D += A_q B_q over ksteps k-steps of 32, from one stage.
-__device__ __forceinline__ void crt_mma_stage(int (&D)[2][2][4], const uint8_t* As, const uint8_t* Bs,
-                                              int arow, int bcol, int g, int ksteps) {
-#pragma unroll 1
-    for (int ks = 0; ks < ksteps; ++ks) {
-        const int c_lo = ((2 * ks) ^ g) * 16, c_hi = ((2 * ks + 1) ^ g) * 16;
-        uint32_t af[2][4], bf[2][2];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const uint8_t* p0 = As + arow + a * 16 * CRT_KB;
-            af[a][0] = *reinterpret_cast<const uint32_t*>(p0 + c_lo);
-            af[a][1] = *reinterpret_cast<const uint32_t*>(p0 + 8 * CRT_KB + c_lo);
-            af[a][2] = *reinterpret_cast<const uint32_t*>(p0 + c_hi);
-            af[a][3] = *reinterpret_cast<const uint32_t*>(p0 + 8 * CRT_KB + c_hi);
-        }
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const uint8_t* p0 = Bs + bcol + b * 8 * CRT_KB;
-            bf[b][0] = *reinterpret_cast<const uint32_t*>(p0 + c_lo);
-            bf[b][1] = *reinterpret_cast<const uint32_t*>(p0 + c_hi);
-        }
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) mma_s8(D[a][b], af[a][0], af[a][1], af[a][2], af[a][3], bf[b][0], bf[b][1]);
-    }
-}
+// The tensor-core update: one 64 x 64 output tile (crt_tile in
+// update_tiles.cuh) per 256-thread block, two blocks per SM.
 
 __global__ void __launch_bounds__(CRT_THREADS, 2)
 update_crt_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, int c0, Field f,
@@ -255,151 +160,28 @@ update_crt_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, in
     extern __shared__ __align__(128) uint8_t smem[];
     const int k = st->k;
     if (k == 0) return;
-    const int r = st->r;
-    const int ksteps = (k + 31) / 32;
-    const int64_t row0 = (int64_t)blockIdx.y * CRT_BM;
-    const int64_t col0 = (int64_t)blockIdx.x * CRT_BN;
-    const int64_t ncols = n - c0;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = warp & 1, wn = warp >> 1;        // 2 x 4 warps of 32 x 16 outputs
-    const int g = lane >> 2, t4 = lane & 3;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t bar0 = sbase + CRT_STAGES * CRT_STAGE_BYTES;
-
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         for (int s = 0; s < CRT_STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    auto issue = [&](int q) {   // residues of modulus q into stage q % CRT_STAGES
-        const int s = q % CRT_STAGES;
-        const uint32_t bar = bar0 + 8 * s;
-        const uint32_t dst = sbase + s * CRT_STAGE_BYTES;
-        mbar_expect_tx(bar, CRT_STAGE_BYTES);
-        bulk_load(dst, Fr + ((int64_t)q * m_pad + row0) * CRT_KB, CRT_A_BYTES, bar);
-        bulk_load(dst + CRT_A_BYTES, Rr + ((int64_t)q * n_pad + col0) * CRT_KB, CRT_B_BYTES, bar);
-    };
-    int issued = 0;   // loads issued so far (thread 0 only)
-    if (tid == 0)
-        for (; issued < CRT_STAGES; ++issued) issue(issued);
+    (void)crt_tile(M, m, n, ld, c0, f, k, st->r, Fr, Rr, m_pad, n_pad, R, ldR, cc, status, spin,
+                   (int64_t)blockIdx.y * CRT_BM, (int64_t)blockIdx.x * CRT_BN, 0, (int)threadIdx.x, smem, sbase, bar0,
+                   BlockBarrier{});
+}
 
-    // byte offsets of this thread's fragments inside a stage (the swizzle
-    // uses row & 7 = g for every row and column the thread touches)
-    const int arow = (wm * 32 + g) * CRT_KB + 4 * t4;
-    const int bcol = (wn * 16 + g) * CRT_KB + 4 * t4;
-    int failed = 0;
-    int q_fail = CRT_L;   // first modulus whose data never arrived
-    // waits for modulus q's stage and runs its GEMM into D (false, on every
-    // thread, if the data never arrived)
-    auto gemm_modulus = [&](int q, int (&D)[2][2][4]) -> bool {
-        const int s = q % CRT_STAGES;
-        if (!mbar_wait(bar0 + 8 * s, (uint32_t)((q / CRT_STAGES) & 1), spin)) failed = 1;
-        if (__syncthreads_or(failed)) {
-            failed = 1;
-            q_fail = q;
-            return false;
-        }
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) D[a][b][e] = 0;
-        crt_mma_stage(D, smem + s * CRT_STAGE_BYTES, smem + s * CRT_STAGE_BYTES + CRT_A_BYTES, arow, bcol, g,
-                      ksteps);
-        return true;
-    };
-
-    // S = sum_i D'_i floor(2^38 / m_i) and X = sum_i D'_i ((M / m_i) mod p),
-    // exact signed 64-bit sums (|S|, |X| < 9 * 2^21 * 2^31 < 2^56)
-    int64_t S[2][2][4], X[2][2][4];
-    int Dc[2][2][4], Dn[2][2][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                S[a][b][e] = 0;
-                X[a][b][e] = 0;
-            }
-    gemm_modulus(0, Dc);
-    // software pipeline over the moduli: the GEMM of modulus q + 1 is issued
-    // before the reconstruction step of modulus q, so the tensor pipe works
-    // while the integer pipe folds D'_q into S and X
-#pragma unroll
-    for (int q = 0; q < CRT_L; ++q) {
-        if (failed) break;
-        if (q + 1 < CRT_L && !gemm_modulus(q + 1, Dn)) break;
-        __syncthreads();   // every warp has read stage q % CRT_STAGES: it may be refilled
-        if (tid == 0 && issued < CRT_L) issue(issued++);
-        const int32_t c38 = (int32_t)cc.c38[q], wp = (int32_t)cc.wp[q];
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    mac_s64(S[a][b][e], Dc[a][b][e], c38);
-                    mac_s64(X[a][b][e], Dc[a][b][e], wp);
-                    Dc[a][b][e] = Dn[a][b][e];
-                }
-    }
-    if (failed) {
-        // wait (bounded) for the copies still in flight into this block's
-        // buffers (loads q_fail .. issued - 1), then report and leave
-        if (tid == 0) {
-            atomicCAS(status, 0, (int)LINAC_ERR_TIMEOUT);
-            for (int j = q_fail; j < issued; ++j)
-                (void)mbar_wait(bar0 + 8 * (j % CRT_STAGES), (uint32_t)((j / CRT_STAGES) & 1), spin);
-        }
-        __syncthreads();
-        return;
-    }
-
-    // step 4 and the write-back: rows of the new pivot block receive R,
-    // every other row C - D mod p
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int64_t row = row0 + wm * 32 + a * 16 + g + hh * 8;
-            if (row >= m) continue;
-            const bool pivot_row = row >= r && row < r + k;
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int64_t col = col0 + wn * 16 + b * 8 + 2 * t4;
-                if (col >= ncols) continue;
-                uint32_t out[2];
-                uint32_t* dst = M + row * ld + c0 + col;
-                const bool pair = col + 1 < ncols;
-                if (pivot_row) {
-                    const int32_t* rr = R + (int64_t)(row - r) * ldR + col;
-                    out[0] = from_balanced(rr[0], f);
-                    out[1] = pair ? from_balanced(rr[1], f) : 0u;
-                } else {
-                    uint32_t cval[2];
-                    if (pair) {
-                        const uint2 cv = *reinterpret_cast<const uint2*>(dst);
-                        cval[0] = cv.x;
-                        cval[1] = cv.y;
-                    } else {
-                        cval[0] = dst[0];
-                        cval[1] = 0;
-                    }
-#pragma unroll
-                    for (int qq = 0; qq < 2; ++qq) {
-                        const int e = hh * 2 + qq;
-                        // beta = nearest integer to S / 2^38 (floor of S / 2^38 + 1/2)
-                        const int64_t beta = (S[a][b][e] + (1LL << 37)) >> 38;
-                        const int64_t x = X[a][b][e] + beta * (int64_t)cc.negMp;
-                        out[qq] = submod(cval[qq], reduce_signed(x, f), f);
-                    }
-                }
-                if (pair) *reinterpret_cast<uint2*>(dst) = make_uint2(out[0], out[1]);
-                else dst[0] = out[0];
-            }
-        }
+// The residue planes of F (m rows) and R' (ncols columns) for one panel.
+linac_status launch_crt_split(const int32_t* Ft, int64_t ldF, int64_t m, const int32_t* R, int64_t ldR,
+                              int64_t ncols, const DenseState* st, const CrtConsts& cc, const CrtScratch* crt,
+                              cudaStream_t stream) {
+    ProfScope ps(stream, PROF_CRT_SPLIT);
+    crt_split_kernel<false><<<(unsigned)(crt->m_pad / 64), 256, 0, stream>>>(Ft, ldF, m, st, cc, crt->Fr, crt->m_pad);
+    crt_split_kernel<true><<<(unsigned)((ncols + 63) / 64), 256, 0, stream>>>(R, ldR, ncols, st, cc, crt->Rr,
+                                                                             crt->n_pad);
+    LINAC_CUDA_TRY(cudaGetLastError());
+    return LINAC_OK;
 }
 
 linac_status launch_update_crt(uint32_t* M, int64_t m, int64_t n, int64_t ld, int c0, const Field& f,
@@ -409,14 +191,9 @@ linac_status launch_update_crt(uint32_t* M, int64_t m, int64_t n, int64_t ld, in
     const int64_t ncols = n - c0;
     if (ncols <= 0 || m <= 0) return LINAC_OK;
     const CrtConsts cc = make_crt(f.p);
-    {
-        ProfScope ps(stream, PROF_CRT_SPLIT);
-        crt_split_kernel<false><<<(unsigned)(crt->m_pad / 64), 256, 0, stream>>>(Ft, ldF, m, st, cc, crt->Fr,
-                                                                                crt->m_pad);
-        crt_split_kernel<true><<<(unsigned)((ncols + 63) / 64), 256, 0, stream>>>(R, ldR, ncols, st, cc, crt->Rr,
-                                                                                 crt->n_pad);
-    }
-    linac_status as = ensure_dynamic_smem((const void*)update_crt_kernel, (int)CRT_SMEM);
+    linac_status as = launch_crt_split(Ft, ldF, m, R, ldR, ncols, st, cc, crt, stream);
+    if (as != LINAC_OK) return as;
+    as = ensure_dynamic_smem((const void*)update_crt_kernel, (int)CRT_SMEM);
     if (as != LINAC_OK) return as;
     dim3 grid((unsigned)((ncols + CRT_BN - 1) / CRT_BN), (unsigned)((m + CRT_BM - 1) / CRT_BM));
     {

@@ -20,9 +20,10 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-LINAC_PATH_AUTO, LINAC_PATH_PLAIN, LINAC_PATH_LIMB, LINAC_PATH_CRT = 0, 1, 2, 3
+LINAC_PATH_AUTO, LINAC_PATH_PLAIN, LINAC_PATH_LIMB, LINAC_PATH_CRT, LINAC_PATH_HYBRID = 0, 1, 2, 3, 4
 LINAC_SHARED_PATTERN = 1
-_PATHS = {"auto": LINAC_PATH_AUTO, "plain": LINAC_PATH_PLAIN, "limb": LINAC_PATH_LIMB, "crt": LINAC_PATH_CRT}
+_PATHS = {"auto": LINAC_PATH_AUTO, "plain": LINAC_PATH_PLAIN, "limb": LINAC_PATH_LIMB, "crt": LINAC_PATH_CRT,
+          "hybrid": LINAC_PATH_HYBRID}
 
 
 class LinacError(RuntimeError):

@@ -66,7 +66,7 @@ def test_misaligned_pointer_rejected(lib):
 def test_bad_options_rejected(lib):
     rank = ctypes.c_int32()
     piv = (ctypes.c_int32 * 8)()
-    for path, nb in ((4, 0), (-1, 0), (0, 20), (0, 256)):
+    for path, nb in ((5, 0), (-1, 0), (0, 20), (0, 256)):
         o = linac.Options(path, nb, 0, 0)
         assert lib.linac_rref_ex(ctypes.c_void_p(0x1000), 4, 4, 4, 2**31 - 1, 4, ctypes.byref(rank), piv,
                                  ctypes.byref(o), None) == 1

@@ -48,7 +48,7 @@ def test_uniform_vs_oracle(shape, p):
 
 
 @pytest.mark.parametrize("nb", [16, 32, 64, 128])
-@pytest.mark.parametrize("path", ["plain", "auto", "limb", "crt"])
+@pytest.mark.parametrize("path", ["plain", "auto", "limb", "crt", "hybrid"])
 def test_panel_widths(nb, path):
     M, _ = synth.rank_deficient(m=333, n=401, d=21, p=P31, seed=nb)
     check_against_oracle(M, P31, nb=nb, path=path)
@@ -248,7 +248,7 @@ def test_crt_and_plain_agree_on_workload_4096():
     assert rc == rp == 4032 and np.array_equal(pc, pp) and np.array_equal(Rc, Rp)
 
 
-@pytest.mark.parametrize("path", ["plain", "crt"])
+@pytest.mark.parametrize("path", ["plain", "crt", "hybrid"])
 def test_rref_replays_in_a_cuda_graph(path):
     """linac_rref is stream-ordered with no host synchronisation: after one
     uncaptured call (which creates the scratch), the call captures into a
@@ -274,3 +274,20 @@ def test_rref_replays_in_a_cuda_graph(path):
         assert int(rank.item()) == r0 == 660
         assert np.array_equal(piv.cpu().numpy()[:r0], piv0)
         assert np.array_equal(A.cpu().numpy().view(np.uint32), R0)
+
+
+@pytest.mark.parametrize("p", [3, 251, 65537, P31, PB, 1431655777])
+@pytest.mark.parametrize("shape", [(37, 45), (300, 300), (513, 700), (1000, 1100), (2100, 2300)])
+def test_hybrid_path_vs_oracle(shape, p):
+    """CUDA-core and multi-modular tiles of one update, taken from one work
+    counter by the two warp groups of each block: the oracle's RREF."""
+    m, n = shape
+    M = synth.uniform(shape, p, synth.stream_key(m * 41 + n, f"hybrid{p}"))
+    check_against_oracle(M, p, path="hybrid")
+
+
+def test_hybrid_and_plain_agree_on_workload_4096():
+    M, _ = synth.rank_deficient()
+    Rh, rh, ph = gpu_rref(M, P31, path="hybrid")
+    Rp, rp, pp = gpu_rref(M, P31, path="plain")
+    assert rh == rp == 4032 and np.array_equal(ph, pp) and np.array_equal(Rh, Rp)

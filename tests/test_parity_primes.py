@@ -118,7 +118,7 @@ def test_rank_deficient_vs_oracle_dense_fold(p):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("path", ["plain", "crt"])
+@pytest.mark.parametrize("path", ["plain", "crt", "hybrid"])
 @pytest.mark.parametrize("nb", [128, 32])
 @pytest.mark.parametrize("p", DENSE_PRIMES + [2**31 - 1])
 def test_balanced_extremes_vs_oracle(p, nb, path):
