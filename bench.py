@@ -51,15 +51,21 @@ P31 = 2**31 - 1
 # 4 schedulers x a 16-lane multiply pipe, two passes per wide multiply-add
 # (ncu: ~4 pipe cycles per 32-thread warp instruction on GB300)
 IMAD_WIDE_PER_SM_CLK = 32
-# DRAM bytes per output of update_plain_kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of the third panel of the
-# 8192 x 8448 elimination: 477.8 MB for 8192 x 8192 outputs; summary in
-# profiles/update_plain_rref_8192x8448.md), valid while the kernel's sources
-# hash to UPDATE_SRC_SHA; the traffic is reported as null otherwise
-UPDATE_BYTES_PER_OUTPUT = 477.8e6 / (8192 * 8192)
-UPDATE_SRC_SHA = "a7542ca4c7ff9976"
-UPDATE_SRC = ["paper_2605_25863_gb300/csrc/update_plain.cu", "paper_2605_25863_gb300/csrc/linac_device.cuh",
-              "paper_2605_25863_gb300/csrc/update.cuh"]
+# DRAM bytes per output of the update kernels from one ncu capture each
+# (dram__bytes_read.sum + dram__bytes_write.sum of one panel's update in the
+# 8192 x 8448 elimination, divided by its outputs; summaries in
+# profiles/update_plain_rref_8192x8448.md and
+# profiles/update_hybrid_rref_8192x8448.md), valid while the kernel's sources
+# hash to the recorded fingerprint; the traffic is reported as null otherwise
+_CSRC = "paper_2605_25863_gb300/csrc/"
+UPDATE_TRAFFIC = {
+    "update_plain": {"bytes_per_output": 478.12e6 / (8192 * 8192), "sha": "4401ada011c488ff",
+                     "files": [_CSRC + f for f in ("update_plain.cu", "update_tiles.cuh", "update.cuh",
+                                                    "linac_device.cuh")]},
+    "update_hybrid": {"bytes_per_output": 504.68e6 / (8192 * 8192), "sha": "76956f08df59e200",
+                      "files": [_CSRC + f for f in ("update_hybrid.cu", "update_tiles.cuh", "update.cuh",
+                                                     "linac_device.cuh")]},
+}
 
 
 def parse():
@@ -71,7 +77,7 @@ def parse():
     ap.add_argument("--m", type=int, default=32768, help="rows (= unknowns) of the dense system")
     ap.add_argument("--rhs", type=int, default=256, help="right-hand-side columns")
     ap.add_argument("--nb", type=int, default=128, help="panel width")
-    ap.add_argument("--path", default="auto", choices=["auto", "plain", "limb", "crt"])
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "limb", "crt", "hybrid"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU oracle, path comparison and batched legs")
@@ -138,10 +144,10 @@ def device_sms_and_max_clock(dev) -> tuple[int, float, str]:
         return sms, clk, "CUDA device clock rate"
 
 
-def update_src_sha() -> str:
+def src_sha(files) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in UPDATE_SRC:
+    for f in files:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -371,7 +377,9 @@ def run_ours(args):
     value, tot_ms = replica_rate(sum(step_ms), work_macs * args.steps, world, dev)
 
     # dominant kernel: the trailing update
-    upd_name = PATH_KERNEL.get(args.path, "update_plain")
+    # the update kernel that ran (LINAC_PATH_AUTO picks by size): the update
+    # class with the largest timed share
+    upd_name = max((k for k in prof if k.startswith("update")), key=lambda k: prof[k][1], default="update_plain")
     upd_launches, upd_ms = prof.get(upd_name, (0, 0.0))
     upd_macs = update_work(m, n, piv, nb) * args.steps
     fold = fold_of(p)
@@ -379,14 +387,24 @@ def run_ours(args):
     imad_per_mac = 1.0 if shift_fold else 1.0 + 2.0 / fold
     achieved = upd_macs / (upd_ms / 1000.0) if upd_ms else 0.0
     traffic = None
-    if upd_name == "update_plain" and upd_launches and update_src_sha() == UPDATE_SRC_SHA:
-        traffic = UPDATE_BYTES_PER_OUTPUT * update_outputs(m, n, nb) * args.steps / upd_launches
+    tr = UPDATE_TRAFFIC.get(upd_name)
+    if tr and tr["bytes_per_output"] and upd_launches and src_sha(tr["files"]) == tr["sha"]:
+        traffic = tr["bytes_per_output"] * update_outputs(m, n, nb) * args.steps / upd_launches
     sms, sm_max_mhz, clk_src = device_sms_and_max_clock(dev)
     peak = sms * IMAD_WIDE_PER_SM_CLK * sm_max_mhz * 1e6 / imad_per_mac
-    s8_peak, u8_peak = imma_peak()
+    rates = imma_peak()
+    s8_peak, u8_peak = rates["imma_s8_mac_per_s"], rates["imma_u8_mac_per_s"]
+    # what the two pipes deliver together: in the probe's mixed block each
+    # group keeps only a fraction of its solo rate (time alone / time together)
+    fi = rates["coissue_imad_only_ms"] / rates["coissue_both_ms"]
+    ft = rates["coissue_imma_only_ms"] / rates["coissue_both_ms"]
+    coissue = rates["imad_wide_per_s"] / imad_per_mac * fi + s8_peak / PATH_NARROW["crt"] * ft
     peaks = {"plain": peak, "plain_basis": f"{sms} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x "
                                            f"{sm_max_mhz:.0f} MHz / {imad_per_mac:.3f} per field MAC",
-             "imma_s8": s8_peak, "imma_u8": u8_peak}
+             "imma_s8": s8_peak, "imma_u8": u8_peak, "coissue": coissue,
+             "coissue_basis": f"measured mad.wide.s32 rate x {fi:.2f} + measured s8 mma.sync rate / 9 x {ft:.2f} "
+                              f"(fractions of each pipe's solo rate kept when 8 warps of each run in one block, "
+                              f"probes/int_rates.cu)"}
     if upd_name == "update_plain":
         roof = {"kernel": upd_name, "bound": "alu", "achieved": achieved / 1e12,
                 "peak": peak / 1e12, "unit": "Tfield-MAC/s", "frac": achieved / peak if peak else None,
@@ -397,6 +415,17 @@ def run_ours(args):
                               f" ({clk_src})"
                               f" / {imad_per_mac:.3f} per field MAC"
                               f" ({'folds on the ALU pipe' if shift_fold else f'fold every {fold} on the multiply pipe'})",
+                "avg_launch_ms": upd_ms / max(1, upd_launches), "launches": upd_launches}
+    elif upd_name == "update_hybrid":   # both pipes at once
+        both = peak + s8_peak / PATH_NARROW["crt"]
+        co = peaks["coissue"]
+        roof = {"kernel": upd_name, "bound": "alu", "achieved": achieved / 1e12, "peak": both / 1e12,
+                "unit": "Tfield-MAC/s", "frac": achieved / both, "traffic": traffic,
+                "traffic_basis": "ncu DRAM bytes per output of the 8192 x 8448 capture x outputs per launch"
+                                 if traffic is not None else "kernel changed since the ncu capture",
+                "peak_basis": "multiply-pipe peak + measured s8 mma.sync rate / 9: both pipes at full rate at "
+                              "once, which this chip does not sustain (coissue_ceiling)",
+                "coissue_ceiling": {"value": co / 1e12, "frac": achieved / co, "basis": peaks["coissue_basis"]},
                 "avg_launch_ms": upd_ms / max(1, upd_launches), "launches": upd_launches}
     else:   # integer tensor pipe: narrow products per second against the measured mma.sync rate
         narrow = PATH_NARROW[args.path]
@@ -518,14 +547,14 @@ def e2e_leg(args, linac, synth, pristine, work, m, n, p, nb, stream, staging=Non
 
 
 def imma_peak():
-    """Measured s8 x s8 -> s32 mma.sync multiply-adds per second of this
-    device (the integer tensor pipe's roofline; probes/int_rates.cu)."""
+    """Measured integer pipe rates of this device (probes/int_rates.cu): the
+    s8 and u8 mma.sync multiply-adds per second (the tensor pipe's roofline),
+    mad.wide.s32 per second, and the co-issue timings."""
     from paper_2605_25863_gb300 import probes
-    r = probes.measure_int_rates()
-    return r["imma_s8_mac_per_s"], r["imma_u8_mac_per_s"]
+    return probes.measure_int_rates()
 
 
-PATH_KERNEL = {"plain": "update_plain", "limb": "update_limb", "crt": "update_crt"}
+PATH_KERNEL = {"plain": "update_plain", "limb": "update_limb", "crt": "update_crt", "hybrid": "update_hybrid"}
 # narrow multiply-adds per field multiply-add: u8 limb products (4 x 4) and
 # s8 residue products (nine moduli)
 PATH_NARROW = {"limb": 16, "crt": 9}
@@ -565,6 +594,12 @@ def time_paths(linac, pristine, work, m, n, p, nb, stream, paths, peaks, reps=2)
             if path == "plain":
                 entry["roofline"] = {"bound": "alu", "peak": peaks["plain"], "frac": rate / peaks["plain"],
                                      "unit": "field MAC/s", "basis": peaks["plain_basis"]}
+            elif path == "hybrid":
+                both = peaks["plain"] + peaks["imma_s8"] / PATH_NARROW["crt"]
+                entry["roofline"] = {"bound": "alu+tensor", "peak": both, "frac": rate / both, "unit": "field MAC/s",
+                                     "basis": "multiply-pipe peak + measured s8 mma.sync rate / 9 (both pipes "
+                                              "at full rate at once, which this chip does not sustain)",
+                                     "coissue_ceiling": peaks["coissue"], "coissue_frac": rate / peaks["coissue"]}
             else:
                 narrow = PATH_NARROW[path]
                 pk = peaks["imma_u8"] if path == "limb" else peaks["imma_s8"]
@@ -581,8 +616,8 @@ def time_paths(linac, pristine, work, m, n, p, nb, stream, paths, peaks, reps=2)
 def path_leg(args, linac, pristine, work, m, n, p, nb, stream, peaks):
     """Plain CUDA-core update vs the multi-modular (CRT, nine s8 residue
     GEMMs) and u8-limb integer-tensor updates on the headline workload."""
-    out = time_paths(linac, pristine, work, m, n, p, nb, stream, ("plain", "crt", "limb"), peaks)
-    for path in ("crt", "limb"):
+    out = time_paths(linac, pristine, work, m, n, p, nb, stream, ("plain", "crt", "hybrid", "limb"), peaks)
+    for path in ("crt", "hybrid", "limb"):
         if "value" in out.get("plain", {}) and "value" in out.get(path, {}):
             out[f"{path}_over_plain"] = out[path]["value"] / out["plain"]["value"]
     return out
@@ -597,7 +632,7 @@ def dense_4096_leg(args, linac, synth, dev, stream, peaks):
     m, n = M.shape
     pristine = linac.to_device(M, dev)
     work = linac.padded(m, n, dev)
-    out = time_paths(linac, pristine, work, m, n, P31, 128, stream, ("plain", "crt", "limb"), peaks, reps=3)
+    out = time_paths(linac, pristine, work, m, n, P31, 128, stream, ("plain", "crt", "hybrid", "limb"), peaks, reps=3)
     for path, e in out.items():
         if "rank" in e:
             e["correct"] = e["rank"] == 4032

@@ -61,7 +61,9 @@ typedef enum {
 /* Trailing-update arithmetic (the rank-k update C <- C - A*B mod p that
  * dominates the O(n^3) work). */
 typedef enum {
-    LINAC_PATH_AUTO = 0,   /* fastest measured path on this device */
+    LINAC_PATH_AUTO = 0,   /* the fastest path measured on GB300 for the size:
+                              LINAC_PATH_HYBRID when m and n are both at least
+                              16384, LINAC_PATH_PLAIN otherwise */
     LINAC_PATH_PLAIN = 1,  /* CUDA cores: lazy signed 64-bit accumulation */
     LINAC_PATH_LIMB = 2,   /* integer tensor pipe: four u8 limbs per residue */
     LINAC_PATH_CRT = 3,    /* integer tensor pipe: residues modulo nine small
@@ -126,7 +128,7 @@ linac_status linac_rref_noalloc(uint32_t *d_A, int64_t m, int64_t n, int64_t ld,
  * linac_rref_host -- linac_rref of a matrix in page-locked HOST memory, with
  * the transfers inside the call: the matrix is copied to library scratch on
  * the device, reduced there exactly as linac_rref reduces it (section 3.2;
- * plain CUDA-core update, default panel width), and copied back in place.
+ * default options), and copied back in place.
  *   h_A       m x n, row-major, leading dimension ld (a multiple of 4, start
  *             16-byte aligned), in page-locked host memory (cudaHostAlloc or
  *             cudaHostRegister); overwritten by its RREF.

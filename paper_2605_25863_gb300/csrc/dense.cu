@@ -230,6 +230,97 @@ window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int
     cluster.sync();   // no block leaves while others may still read its shared memory
 }
 
+// The same pivot window on one block, for panels of at most WIN1_NB columns
+// (small matrices): the window's w + WIN_EXTRA rows fit one block's shared
+// memory, and a block barrier per column costs far less than the cluster
+// barrier.  Per column one block-wide minimum (two alternating slots, one
+// barrier) finds the pivot, and the pass that eliminates the column also
+// looks for the next column's lowest candidate.  Outputs as window_kernel.
+__global__ void __launch_bounds__(WIN1_THREADS)
+window1_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f, DenseState* st,
+               uint32_t* __restrict__ panelU, int G, const int32_t* __restrict__ rowmap) {
+    constexpr int ROWS = WIN1_NB + WIN_EXTRA, SW = WIN1_NB + 1;
+    __shared__ __align__(16) uint32_t P[ROWS * SW];
+    __shared__ int red[2][WIN1_THREADS / 32];
+    __shared__ unsigned char isp[ROWS];
+    __shared__ int own[WIN1_NB], Jc[WIN1_NB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t r = st->r;
+    const int64_t left = m - r > 0 ? m - r : 0;
+    const int rows = (int)(left < w + WIN_EXTRA ? left : w + WIN_EXTRA);
+    int buf = 0;
+    auto block_min = [&](int v) -> int {   // one barrier; slots alternate so a slot is rewritten after another barrier
+        v = __reduce_min_sync(0xffffffffu, v);
+        if (lane == 0) red[buf][warp] = v;
+        __syncthreads();
+        int x = INT_MAX;
+#pragma unroll
+        for (int i = 0; i < WIN1_THREADS / 32; ++i) x = min(x, red[buf][i]);
+        buf ^= 1;
+        return x;
+    };
+    int cand = INT_MAX;
+    for (int e = tid; e < rows * w; e += WIN1_THREADS) {
+        const int i = e / w, j = e - i * w;
+        const uint32_t v = M[map_row(rowmap, r, i) * ld + c0 + j];
+        P[i * SW + j] = to_mont(v, f);
+        if (j == 0 && v != 0u && i < cand) cand = i;
+    }
+    for (int i = tid; i < ROWS; i += WIN1_THREADS) isp[i] = 0;
+    int q = block_min(cand);   // also the barrier after the load
+    int kk = 0;
+    for (int cc = 0; cc < w; ++cc) {
+        if (q != INT_MAX) {
+            if (tid == 0) {
+                isp[q] = 1;
+                own[kk] = q;
+                Jc[kk] = cc;
+            }
+            ++kk;
+        }
+        // fraction-free elimination of column cc from the other remaining
+        // rows (row_i <- h row_i - f_i row_q on the columns right of cc), and
+        // the next column's candidate from the updated entries
+        const int nc = w - cc - 1;
+        cand = INT_MAX;
+        if (nc > 0) {
+            const uint32_t h = q != INT_MAX ? P[q * SW + cc] : 0u;
+            for (int e = tid; e < rows * nc; e += WIN1_THREADS) {
+                const int i = e / nc, j = cc + 1 + (e - i * nc);
+                if (i == q || isp[i]) continue;
+                uint32_t x = P[i * SW + j];
+                if (q != INT_MAX) {
+                    const uint32_t fi = P[i * SW + cc];
+                    if (fi != 0u) {
+                        x = mont_mul2add(h, x, f.p - fi, P[q * SW + j], f);
+                        P[i * SW + j] = x;
+                    }
+                }
+                if (j == cc + 1 && x != 0u && i < cand) cand = i;
+            }
+            q = block_min(cand);
+        }
+    }
+    __syncthreads();   // the last column's pivot record is visible to every thread
+    if (kk == w || rows == left) {
+        for (int t = tid; t < kk; t += WIN1_THREADS) {
+            st->Pi[t] = (int32_t)map_row(rowmap, r, own[t]);
+            st->J[t] = c0 + Jc[t];
+        }
+        for (int e = tid; e < kk * w; e += WIN1_THREADS) {
+            const int t = e / w, j = e - t * w;
+            panelU[(size_t)t * NB_MAX + j] = mont_redc(P[own[t] * SW + j], f);
+        }
+        if (tid == 0) {
+            st->k = kk;
+            st->win_ok = 1;
+            atomicAdd(&st->bar.count, (unsigned)w * (unsigned)G);
+        }
+    } else if (tid == 0) {
+        st->win_ok = 0;
+    }
+}
+
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, int S_max,
              Field f, DenseState* st, uint32_t* cand, uint32_t* panelU, int* status, WaitLimit wl,
@@ -747,7 +838,7 @@ linac_status dense_rref(uint32_t* dA, int64_t m, int64_t n, int64_t ld, const Fi
         const int64_t ncols = n - c0;
         {
             ProfScope ps(stream, PROF_PANEL);
-            window_kernel<<<WIN_CTAS, WIN_THREADS, 0, stream>>>(dA, m, ld, (int)c0, w, f, st, panelU, G, nullptr);
+            launch_window(dA, m, ld, (int)c0, w, f, st, panelU, G, nullptr, stream);
         }
         {
             const uint32_t* Mc = dA;

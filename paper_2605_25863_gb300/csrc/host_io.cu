@@ -91,7 +91,7 @@ extern "C" linac_status linac_rref_host(uint32_t* h_A, int64_t m, int64_t n, int
     if (!st) return LINAC_ERR_NOMEM;
     LINAC_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int), stream));
     if ((s = copy_words(dA_h, dA, abytes, stream)) != LINAC_OK) return s;
-    s = dense_rref(dA, m, n, ld, f, n, d_rank, d_piv, LINAC_PATH_PLAIN, 0, stream);
+    s = dense_rref(dA, m, n, ld, f, n, d_rank, d_piv, auto_path(m, n), 0, stream);
     if (s != LINAC_OK) return s;
     if ((s = copy_words(dA, dA_h, abytes, stream)) != LINAC_OK) return s;
     {

@@ -63,6 +63,9 @@ WaitLimit wait_limit();
 // call after the first of each size.
 linac_status ensure_dynamic_smem(const void* fn, int bytes);
 
+// The trailing-update path LINAC_PATH_AUTO selects for an m x n elimination.
+int auto_path(int64_t m, int64_t n);
+
 // Number of SMs on the current device (cached per device).
 int sm_count();
 // Opt-in shared memory per block of the current device in bytes (cached per

@@ -353,7 +353,7 @@ linac_status lup_factor(const uint32_t* dA, int64_t m, int64_t n, int64_t ldA, c
         const int64_t ncols = n - c0;
         {
             ProfScope ps(stream, PROF_PANEL);
-            window_kernel<<<WIN_CTAS, WIN_THREADS, 0, stream>>>(Wm, m, L.ldw, (int)c0, w, f, st, panelU, G, list_cur);
+            launch_window(Wm, m, L.ldw, (int)c0, w, f, st, panelU, G, list_cur, stream);
         }
         {
             const uint32_t* Mc = Wm;

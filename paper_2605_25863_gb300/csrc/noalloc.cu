@@ -158,7 +158,7 @@ extern "C" linac_status linac_rref_noalloc(uint32_t* d_A, int64_t m, int64_t n, 
     for (int64_t c0 = 0; c0 < n; c0 += nb) {
         const int w = (int)std::min<int64_t>(nb, n - c0);
         const int64_t ncols = n - c0;
-        window_kernel<<<WIN_CTAS, WIN_THREADS, 0, stream>>>(d_A, m, ld, (int)c0, w, f, st, panelU, G, nullptr);
+        launch_window(d_A, m, ld, (int)c0, w, f, st, panelU, G, nullptr, stream);
         {
             const uint32_t* Mc = d_A;
             int64_t m_ = m, ld_ = ld;

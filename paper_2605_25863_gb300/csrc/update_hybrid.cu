@@ -34,7 +34,7 @@ namespace {
 
 constexpr int HY_THREADS = 512;
 constexpr int HY_GROUP = 256;
-constexpr size_t HY_SMEM = CRT_SMEM;   // the multi-modular group's ring (the plain group's tiles are static)
+constexpr size_t HY_SMEM = CRT_SMEM;   // the multi-modular group's ring (plain_tile's arrays are static)
 
 template <int FOLD, int SHIFTS>
 __global__ void __launch_bounds__(HY_THREADS, 1)
@@ -43,8 +43,6 @@ update_hybrid_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld,
                      const int32_t* __restrict__ R, int64_t ldR, const uint8_t* __restrict__ Fr,
                      const uint8_t* __restrict__ Rr, int64_t m_pad, int64_t n_pad, CrtConsts cc, int* status,
                      long long spin, unsigned int* __restrict__ next_area) {
-    __shared__ __align__(16) int32_t As[2 * UPD_BK * UPD_BM];
-    __shared__ __align__(16) int32_t Bs[2 * UPD_BK * UPD_BN2];
     __shared__ int s_area[2];
     extern __shared__ __align__(128) uint8_t smem[];
     const int k = st->k;
@@ -67,7 +65,7 @@ update_hybrid_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld,
         for (int a; (a = next(0, bar)) >= 0;) {
             const int64_t row0 = (int64_t)(a / tiles_x) * UPD_BM, col0 = (int64_t)(a % tiles_x) * UPD_BN2;
             plain_tile<FOLD, SHIFTS, 0>(M, m, n, ld, c0, f, fs, k, r, Ft, ldF, R, ldR, nullptr, 0, nullptr, row0,
-                                        col0, tid, As, Bs, bar);
+                                        col0, tid, bar);
         }
     } else {
         const NamedBarrier bar{2, HY_GROUP};

@@ -26,8 +26,6 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
                     FoldShifts fs, const DenseState* __restrict__ st, const int32_t* __restrict__ Ft,
                     int64_t ldF, const int32_t* __restrict__ R, int64_t ldR, int32_t* __restrict__ Out,
                     int64_t ldOut, const int32_t* __restrict__ rowmap) {
-    __shared__ __align__(16) int32_t As[2 * UPD_BK * UPD_BM];
-    __shared__ __align__(16) int32_t Bs[2 * UPD_BK * UPD_BN2];
     const int k = st->k;
     if (k == 0) return;
     const int r = st->r;
@@ -38,7 +36,7 @@ update_plain_kernel(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, 
     }
     const int64_t col0 = (int64_t)blockIdx.x * UPD_BN2;   // relative to c0
     plain_tile<FOLD, SHIFTS, MODE>(M, m, n, ld, c0, f, fs, k, r, Ft, ldF, R, ldR, Out, ldOut, rowmap, row0, col0,
-                                   (int)threadIdx.x, As, Bs, BlockBarrier{});
+                                   (int)threadIdx.x, BlockBarrier{});
 }
 
 namespace {

@@ -56,16 +56,19 @@ struct NamedBarrier {
 // products stay below 2^63.  One reduction per output and panel finishes:
 // two more folds and conditional subtractions when 2^32 mod p is sparse
 // (reduce_alu), Barrett otherwise.  K in chunks of 16 staged by cp.async
-// double buffering in As (2 x 16 x 128) and Bs (2 x 16 x 64).
+// double buffering in the function's own shared arrays As (2 x 16 x 128) and
+// Bs (2 x 16 x 64).  (Three stages with one barrier per chunk were measured
+// and were no faster, alone or beside the multi-modular warps.)
 template <int FOLD, int SHIFTS, int MODE, class Bar>
 __device__ __forceinline__ void plain_tile(uint32_t* __restrict__ M, int64_t m, int64_t n, int64_t ld, int c0,
                                            const Field& f, const FoldShifts& fs, int k, int r,
                                            const int32_t* __restrict__ Ft, int64_t ldF,
                                            const int32_t* __restrict__ R, int64_t ldR, int32_t* __restrict__ Out,
                                            int64_t ldOut, const int32_t* __restrict__ rowmap, int64_t row0,
-                                           int64_t col0, int tid, int32_t* __restrict__ As,
-                                           int32_t* __restrict__ Bs, Bar bar) {
+                                           int64_t col0, int tid, Bar bar) {
     static_assert(UPD_BK % FOLD == 0, "fold cadence must divide the K chunk");
+    __shared__ __align__(16) int32_t As[2][UPD_BK][UPD_BM];
+    __shared__ __align__(16) int32_t Bs[2][UPD_BK][UPD_BN2];
     const int kpad = (k + UPD_BK - 1) / UPD_BK * UPD_BK;
     const int64_t ncols = n - c0;
     const int tx = tid & 15, ty = tid >> 4;
@@ -78,14 +81,14 @@ __device__ __forceinline__ void plain_tile(uint32_t* __restrict__ M, int64_t m, 
             const int64_t row = row0 + x4;
             const int bytes = row + 4 <= m ? 16 : (row < m ? (int)(m - row) * 4 : 0);
             const int32_t* src = bytes ? Ft + (int64_t)(k0 + kk) * ldF + row : Ft;
-            cp_async16(&As[(stage * UPD_BK + kk) * UPD_BM + x4], src, bytes);
+            cp_async16(&As[stage][kk][x4], src, bytes);
         }
         {
             const int kk = tid >> 4, x4 = (tid & 15) * 4;
             const int64_t col = col0 + x4;
             const int bytes = col + 4 <= ncols ? 16 : (col < ncols ? (int)(ncols - col) * 4 : 0);
             const int32_t* src = bytes ? R + (int64_t)(k0 + kk) * ldR + col : R;
-            cp_async16(&Bs[(stage * UPD_BK + kk) * UPD_BN2 + x4], src, bytes);
+            cp_async16(&Bs[stage][kk][x4], src, bytes);
         }
         cp_async_commit();
     };
@@ -109,11 +112,9 @@ __device__ __forceinline__ void plain_tile(uint32_t* __restrict__ M, int64_t m, 
         const int s = kt & 1;
 #pragma unroll
         for (int kk = 0; kk < UPD_BK; ++kk) {
-            const int32_t* arow = As + (s * UPD_BK + kk) * UPD_BM;
-            const int32_t* brow = Bs + (s * UPD_BK + kk) * UPD_BN2;
-            const int4 a0 = *reinterpret_cast<const int4*>(arow + ty * 4);
-            const int4 a1 = *reinterpret_cast<const int4*>(arow + 64 + ty * 4);
-            const int4 b0 = *reinterpret_cast<const int4*>(brow + tx * 4);
+            const int4 a0 = *reinterpret_cast<const int4*>(&As[s][kk][ty * 4]);
+            const int4 a1 = *reinterpret_cast<const int4*>(&As[s][kk][64 + ty * 4]);
+            const int4 b0 = *reinterpret_cast<const int4*>(&Bs[s][kk][tx * 4]);
             const int a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const int b[4] = {b0.x, b0.y, b0.z, b0.w};
 #pragma unroll
