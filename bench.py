@@ -51,6 +51,12 @@ P31 = 2**31 - 1
 # 4 schedulers x a 16-lane multiply pipe, two passes per wide multiply-add
 # (ncu: ~4 pipe cycles per 32-thread warp instruction on GB300)
 IMAD_WIDE_PER_SM_CLK = 32
+# DRAM bytes moved by the batched kernels per byte of the batch's matrices
+# (ncu: 1.627 + 1.875 GB and 0.024 + 0.0002 GB read + written by the two
+# launches of the 2000-system uneven batch, whose matrices hold 0.385 GB;
+# summary in profiles/batched_uneven_bucket512.md)
+BATCHED_DRAM_PER_MATRIX_BYTE = 3.527e9 / 0.3854e9
+
 # DRAM bytes per output of the update kernels from one ncu capture each
 # (dram__bytes_read.sum + dram__bytes_write.sum of one panel's update in the
 # 8192 x 8448 elimination, divided by its outputs; summaries in
@@ -766,9 +772,32 @@ def batched_leg(args, linac, synth, dev, stream):
     ok = bool((rk == B.nA - B.deficiency).all())
     macs = sum((int(B.m[s]) - 1) * (int(B.n[s]) * int(rk[s]) - int(rk[s]) * (int(rk[s]) + 1) // 2)
                for s in range(B.count))
+    rate = macs / (ms / 1000.0)
+    peak = batched_peak(dev, B.p)
+    words = int((B.m.astype(np.int64) * B.ld.astype(np.int64)).sum())
     return {"systems": B.count, "systems_per_s": B.count / (ms / 1000.0), "ms": ms, "panel_widths": widths,
-            "field_macs_per_s_approx": macs / (ms / 1000.0), "ranks_ok": ok, "launch": "cuda_graph",
+            "field_macs_per_s_approx": rate, "ranks_ok": ok, "launch": "cuda_graph",
+            "roofline": {"bound": "alu", "achieved": rate, "peak": peak["value"], "frac": rate / peak["value"],
+                         "unit": "field MAC/s", "basis": peak["basis"],
+                         "dram_bytes_per_system": BATCHED_DRAM_PER_MATRIX_BYTE * words * 4 / B.count,
+                         "one_read_and_write_bytes_per_system": 2 * words * 4 / B.count,
+                         "dram_basis": "ncu DRAM bytes of the 2000-system capture per byte of its matrices "
+                                       "(profiles/batched_uneven_bucket512.md) x this batch's matrix bytes"},
             "workload": "batched uneven [A|B], n log-uniform [32,512], 4 RHS, p = 2^31 - 19"}
+
+
+def batched_peak(dev, p):
+    """The multiply-pipe roofline of the batched kernel for prime p: one
+    mad.wide.s32 per field MAC plus its folds (on the multiply pipe unless
+    2^32 mod p is a single power of two, the batched kernel's rule)."""
+    sms, mhz, src = device_sms_and_max_clock(dev)
+    c32 = (1 << 32) % p
+    single = c32 & (c32 - 1) == 0
+    fold = fold_of(p)
+    per = 1.0 if single else 1.0 + 2.0 / fold
+    return {"value": sms * IMAD_WIDE_PER_SM_CLK * mhz * 1e6 / per,
+            "basis": f"{sms} SMs x {IMAD_WIDE_PER_SM_CLK} mad.wide.s32/clk x {mhz:.0f} MHz / {per:.3f} per field MAC"
+                     f" ({'shift fold' if single else f'fold every {fold} on the multiply pipe'})"}
 
 
 def shared_leg(args, linac, synth, dev, stream):
