@@ -41,10 +41,10 @@ constexpr int BT_WINDOW = 8;          // rows of the pivot window beyond the pan
 
 // The pivot window's slab: bt_win_rows rows of 2 NB + 1 words (NB panel
 // entries, NB coefficients over the pivot rows, one pad word against bank
-// conflicts), then two per-row scale factors.
+// conflicts).
 __host__ __device__ constexpr int bt_win_rows(int nb) { return nb + BT_WINDOW; }
 __host__ __device__ constexpr size_t bt_win_bytes(int nb) {
-    return ((size_t)bt_win_rows(nb) * (2 * nb + 1) + 2 * (size_t)bt_win_rows(nb)) * 4;
+    return (size_t)bt_win_rows(nb) * (2 * nb + 1) * 4;
 }
 
 // Per-call device scratch of the batched driver.
@@ -127,8 +127,9 @@ struct BtSmall {
     int J[NB], Pi[NB], own[NB], srcs[NB], dsts[NB], colt[NB];
     uint32_t hinv[NB], hs[NB];
     int red[BT_THREADS / 32];
-    int red2[2][BT_THREADS / 32];
+    alignas(16) int red2[2][BT_THREADS / 32];
     int s_min, s_sys, s_npairs, s_fail, s_pat;
+    uint32_t s_inv;
 };
 
 // Block-wide minimum of one int per thread (INT_MAX = none).
@@ -153,14 +154,14 @@ __device__ __forceinline__ int block_min(int v, BtSmall<NB>& sm) {
 // read it.
 template <int NB>
 __device__ __forceinline__ int block_min1(int v, BtSmall<NB>& sm, int& buf) {
+    static_assert(BT_THREADS == 256, "eight warp minima, read as two 16-byte words");
     v = __reduce_min_sync(0xffffffffu, v);
     if ((threadIdx.x & 31) == 0) sm.red2[buf][threadIdx.x >> 5] = v;
     __syncthreads();
-    int x = INT_MAX;
-#pragma unroll
-    for (int i = 0; i < BT_THREADS / 32; ++i) x = min(x, sm.red2[buf][i]);
+    const int4 a = *reinterpret_cast<const int4*>(&sm.red2[buf][0]);
+    const int4 b = *reinterpret_cast<const int4*>(&sm.red2[buf][4]);
     buf ^= 1;
-    return x;
+    return min(min(min(a.x, a.y), min(a.z, a.w)), min(min(b.x, b.y), min(b.z, b.w)));
 }
 
 // Fold cadence of the lazy accumulators (fold after products t with
@@ -179,61 +180,84 @@ struct BtFold {
 // Window row i is A row r + i (forced = 0: pivot search, the lowest row with
 // a nonzero entry in the column) or A row sm.Pi[i] (forced = 1: the pivot rows
 // and columns sm.Pi[t], sm.J[t] of a previous search, in order; rows = k).
-// Every row keeps
-//     current row i = sig_i * (original row i) + sum_u a_iu * (original pivot row u)
-// with the coefficients a_iu in slab columns NB + u.  A column cc with a pivot
-// (row q, pivot number s, head h = row_q[cc]) sets a_qs = sig_q, then
-// replaces every other row i with f = row_i[cc] != 0 -- earlier pivot rows
-// included -- by h * row_i - f * row_q on the panel columns right of cc and on
-// the coefficients 0..s; the factor h also goes into sig_i, or into the head
-// hd_i of an earlier pivot row.  At the end pivot row t is zero at every other
-// pivot column and hd_t at its own, so E[t][u] = a_{t u} / hd_t gives E G = I.
+// A column cc with a pivot (row q, pivot number s, head h_s = row_q[cc])
+// replaces EVERY other row i -- earlier pivot rows, and rows whose entry
+// f = row_i[cc] is zero, included -- by h_s * row_i - f * row_q, on the panel
+// columns right of cc and on the coefficients 0..s (slab columns NB + u).
+// Because every row is scaled alike, the bookkeeping has a closed form: with
+// H_s = h_0 h_1 ... h_{s-1},
+//     current row i = H_s * (original row i) + sum_u a_iu * (original pivot row u)
+// for every row that is not yet a pivot row, so pivot row s takes a_ss = H_s;
+// and at the end pivot row t is zero at every other pivot column and holds
+// hd_t = h_t h_{t+1} ... h_{k-1} = H_k / H_t at its own, so
+// E[t][u] = a_tu / hd_t = a_tu H_t / H_k gives E G = I.  No per-row scale is
+// stored, no row branches on its entry f, and one inverse (of H_k) serves the
+// whole panel.
 //
 // The slab holds every value in Montgomery form (x R mod p, R = 2^32), so each
 // update h * row_i - f * row_q is two 32 x 32 products and one Montgomery
-// reduction; zero tests are unaffected, and E[t][u] = a_{t u} / hd_t is the
-// same from the held values because the factors R cancel.
+// reduction (f = 0 enters as p - 0 = p: h x + p y < 2 p^2 < p R still holds);
+// zero tests are unaffected.  The products H_s are held the same way.
 //
 // The w - cc - 1 panel columns and s + 1 <= cc + 1 coefficients that change
 // at column cc fit in NB slab columns, so the block is laid out as NB
 // columns by BT_THREADS / NB row groups, and column slot cp of a thread names
-// panel column cc + 1 + cp, or coefficient cp - (w - cc - 1).
+// panel column cc + 1 + cp, or coefficient cp - (w - cc - 1).  A thread keeps
+// the pivot flags of its own rows in one register.
 //
 // Returns the number of pivots k, or -1 in forced mode when a given pivot
 // vanished.  Unless forced mode, k == w or keep != 0, E is not needed and is
 // not formed; otherwise Et[u * NB + t] = balanced E[t][u] for t, u < k
-// rounded up to 4, zero padded.  Fills sm.J, sm.Pi, sm.own (search).
+// rounded up to 4, zero padded.  Fills sm.J, sm.Pi, sm.own (search) and
+// sm.hs[t] = H_t (held form).
 template <int NB>
 __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int64_t ld, int r, int c0, int w, int rows,
-                            int forced, int keep, const Field& f, uint32_t* G, unsigned char* isp,
-                            BtSmall<NB>& sm, int32_t* Et) {
+                            int forced, int keep, const Field& f, uint32_t* __restrict__ G,
+                            BtSmall<NB>& sm, int32_t* __restrict__ Et) {
     constexpr int SWG = 2 * NB + 1;
     constexpr int CW = NB;                  // column slots
     constexpr int RGN = BT_THREADS / CW;    // row groups
     constexpr int UMAX = (bt_win_rows(NB) + RGN - 1) / RGN;
     constexpr int U = UMAX < 6 ? UMAX : 6;  // rows per batch of independent updates
     static_assert(BT_THREADS % CW == 0, "column slots must divide the block");
+    static_assert(UMAX <= 32, "the pivot flags of a thread's rows fit one word");
     const int tid = threadIdx.x;
     const int cp = tid % CW, rg = tid / CW;
-    uint32_t* sig = G + bt_win_rows(NB) * SWG;
-    uint32_t* hd = sig + bt_win_rows(NB);
+    // load: the panel entries in Montgomery form, coefficients zero; up to 8
+    // loads of a thread in flight at once
+    constexpr int LPT = (bt_win_rows(NB) * NB + BT_THREADS - 1) / BT_THREADS;
+    constexpr int LB = LPT < 8 ? LPT : 8;
+    const int nload = rows * NB;
     int cand = INT_MAX;
-    for (int e = tid; e < rows * 2 * NB; e += BT_THREADS) {
-        const int i = e / (2 * NB), c = e % (2 * NB);
-        const int64_t arow = forced ? (int64_t)sm.Pi[i] : (int64_t)(r + i);
-        const uint32_t v = c < w ? A[arow * ld + c0 + c] : 0u;
-        G[i * SWG + c] = to_mont(v, f);
-        if (c == 0) {
-            sig[i] = f.c32;   // R mod p: the held form of 1
-            hd[i] = 0u;
-            isp[i] = 0;
-            if (v != 0u && i < cand) cand = i;
+    for (int e = tid; e < nload; e += BT_THREADS) G[(e / NB) * SWG + NB + e % NB] = 0u;
+    for (int e0 = 0; e0 < nload; e0 += LB * BT_THREADS) {
+        uint32_t v[LB];
+#pragma unroll
+        for (int b = 0; b < LB; ++b) {
+            const int e = e0 + b * BT_THREADS + tid;
+            v[b] = 0u;
+            if (e < nload) {
+                const int i = e / NB, c = e % NB;
+                const int64_t arow = forced ? (int64_t)sm.Pi[i] : (int64_t)(r + i);
+                if (c < w) v[b] = A[arow * ld + c0 + c];
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < LB; ++b) {
+            const int e = e0 + b * BT_THREADS + tid;
+            if (e < nload) {
+                const int i = e / NB, c = e % NB;
+                G[i * SWG + c] = to_mont(v[b], f);
+                if (c == 0 && v[b] != 0u && i < cand) cand = i;
+            }
         }
     }
     int buf = 0;
     int q = INT_MAX;
     if (forced) __syncthreads();
     else q = block_min1<NB>(cand, sm, buf);   // also the barrier after the load
+    uint32_t Hs = f.c32;   // H_0 = 1, held form R mod p
+    uint32_t pmask = 0;    // bit j: window row rg + j RGN is a pivot row
     int s = 0;
     for (int cc = 0; cc < w; ++cc) {
         int qq = -1;   // window row of this column's pivot
@@ -244,70 +268,81 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
             qq = q;
         }
         const bool has = qq >= 0;
-        uint32_t h = 0u, sq = 0u;
-        if (has) {
-            h = G[qq * SWG + cc];
-            sq = sig[qq];
-            if (h == 0u) return -1;   // forced mode only (a found pivot is nonzero); uniform
-            if (!forced && tid == 0) {
-                isp[qq] = 1;
-                sm.J[s] = c0 + cc;
-                sm.Pi[s] = r + qq;
-                sm.own[s] = qq;
-            }
-        }
+        const uint32_t h = has ? G[qq * SWG + cc] : 0u;
+        if (has && qq % RGN == rg) pmask |= 1u << (qq / RGN);
         const int np = w - cc - 1;
         int col = -1;
         if (cp < np) col = cc + 1 + cp;
         else if (has && cp - np <= s) col = NB + (cp - np);
         const bool act = has && col >= 0;
         const bool col_s = has && col == NB + s;
-        const uint32_t pv = col_s ? sq : (act ? G[qq * SWG + col] : 0u);
+        const uint32_t pv = col_s ? Hs : (act ? G[qq * SWG + col] : 0u);
         const bool cand_col = !forced && cp == 0 && np > 0;   // col == cc + 1
         cand = INT_MAX;
         if (act || cand_col) {
-            for (int i0 = rg; i0 < rows; i0 += U * RGN) {
+            for (int i0 = rg, j0 = 0; i0 < rows; i0 += U * RGN, j0 += U) {
                 uint32_t x[U], fi[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int i = i0 + u * RGN;
-                    const bool ok = i < rows && i != qq;
-                    fi[u] = (ok && has) ? G[i * SWG + cc] : 0u;
-                    x[u] = ok ? G[i * SWG + col] : 0u;
+                    fi[u] = (i < rows && act) ? G[i * SWG + cc] : 0u;
+                    x[u] = i < rows ? G[i * SWG + col] : 0u;
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int i = i0 + u * RGN;
-                    if (act && fi[u] != 0u) {
+                    if (act && i < rows && i != qq) {
                         x[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
                         G[i * SWG + col] = x[u];
-                        if (col_s) {
-                            const bool prow = forced ? i < s : isp[i] != 0;
-                            if (prow) hd[i] = mont_mul(h, hd[i], f);
-                            else sig[i] = mont_mul(h, sig[i], f);
-                        }
                     }
-                    if (cand_col && x[u] != 0u && i < rows && i != qq && !isp[i] && i < cand) cand = i;
+                }
+                if (cand_col) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int i = i0 + u * RGN;
+                        if (i < rows && x[u] != 0u && !((pmask >> (j0 + u)) & 1u) && i < cand) cand = i;
+                    }
                 }
             }
         }
-        if (col_s && qq % RGN == rg) {
-            G[qq * SWG + col] = sq;
-            hd[qq] = h;
+        if (has) {
+            if (col_s && qq % RGN == rg) G[qq * SWG + col] = Hs;
+            if (tid == 0) {
+                sm.hs[s] = Hs;
+                if (!forced) {
+                    sm.J[s] = c0 + cc;
+                    sm.Pi[s] = r + qq;
+                    sm.own[s] = qq;
+                }
+            }
+            Hs = mont_mul(h, Hs, f);
+            ++s;
         }
-        if (has) ++s;
+        // forced mode: a reused pivot that vanished ends the panel (h is the
+        // same in every thread, so the whole block returns; a pivot found by
+        // the search is nonzero)
+        if (forced && h == 0u) return -1;
         if (!forced && cc + 1 < w) q = block_min1<NB>(cand, sm, buf);
         else __syncthreads();
     }
     const int k = s;
     if (!forced && k < w && !keep) return k;
-    for (int t = tid; t < k; t += BT_THREADS) sm.hinv[t] = inverse_fermat(hd[forced ? t : sm.own[t]], f);
+    // 1 / (hd_t R) = H_t / (H_k R): one inverse of the held H_k, then one
+    // Montgomery product by the held H_t per pivot
+    if (tid < 32) {
+        const uint32_t inv = inverse_fermat(Hs, f);
+        if (tid == 0) sm.s_inv = inv;
+    }
     __syncthreads();
+    const uint32_t invH = sm.s_inv;
     const int kp = (k + 3) & ~3;
     for (int e = tid; e < kp * kp; e += BT_THREADS) {
         const int u = e / kp, t = e % kp;
         int32_t v = 0;
-        if (t < k && u < k) v = to_balanced(mulmod(G[(forced ? t : sm.own[t]) * SWG + NB + u], sm.hinv[t], f), f);
+        if (t < k && u < k) {
+            const uint32_t hinv = mont_mul(sm.hs[t], invH, f);
+            v = to_balanced(mulmod(G[(forced ? t : sm.own[t]) * SWG + NB + u], hinv, f), f);
+        }
         Et[u * NB + t] = v;
     }
     __syncthreads();
@@ -360,7 +395,7 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             // record.
             const int rows_all = m - r;
             const int wrows = min(rows_all, w + BT_WINDOW);
-            k = bt_window_gj<NB>(A, ld, r, c0, w, wrows, 0, wrows == rows_all, f, P, isp, sm, Et);
+            k = bt_window_gj<NB>(A, ld, r, c0, w, wrows, 0, wrows == rows_all, f, P, sm, Et);
             e_ready = k == w || wrows == rows_all;
             if (!e_ready) {
                 const int rows = rows_all;
@@ -431,7 +466,7 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             }
             if (tid == 0) sm.s_fail = 0;
             __syncthreads();
-            if (bt_window_gj<NB>(A, ld, r, c0, w, k, 1, 1, f, P, isp, sm, Et) < 0) return false;
+            if (bt_window_gj<NB>(A, ld, r, c0, w, k, 1, 1, f, P, sm, Et) < 0) return false;
         }
         if (k == 0) continue;
         // multipliers F (original entries at the pivot columns, all of which lie
@@ -444,22 +479,39 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
         __syncthreads();
         {
             const int wq = (w + 3) >> 2;
-#pragma unroll 2
-            for (int e = tid; e < m * wq; e += BT_THREADS) {
-                const int i = e / wq, q = e - i * wq;
-                const uint32_t* src = A + (int64_t)i * ld + c0 + 4 * q;
-                uint32_t v4[4];
-                if (vec_ok && 4 * q + 4 <= w) {
-                    const uint4 u = *reinterpret_cast<const uint4*>(src);
-                    v4[0] = u.x; v4[1] = u.y; v4[2] = u.z; v4[3] = u.w;
-                } else {
+            const int nq = m * wq;
+            constexpr int FB = 4;   // 16-byte loads of a thread in flight at once
+            for (int e0 = tid; e0 < nq; e0 += FB * BT_THREADS) {
+                uint4 v[FB];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) v4[u] = 4 * q + u < w ? src[u] : 0u;
+                for (int b = 0; b < FB; ++b) {
+                    const int e = e0 + b * BT_THREADS;
+                    v[b] = make_uint4(0u, 0u, 0u, 0u);
+                    if (e < nq) {
+                        const int i = e / wq, q = e - i * wq;
+                        const uint32_t* src = A + (int64_t)i * ld + c0 + 4 * q;   // 4 q < w
+                        if (vec_ok && 4 * q + 4 <= w) {
+                            v[b] = *reinterpret_cast<const uint4*>(src);
+                        } else {
+                            v[b].x = src[0];
+                            v[b].y = 4 * q + 1 < w ? src[1] : 0u;
+                            v[b].z = 4 * q + 2 < w ? src[2] : 0u;
+                            v[b].w = 4 * q + 3 < w ? src[3] : 0u;
+                        }
+                    }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int t = 4 * q + u < w ? sm.colt[4 * q + u] : -1;
-                    if (t >= 0) Ft[t * ldF + i] = to_balanced(v4[u], f);
+                for (int b = 0; b < FB; ++b) {
+                    const int e = e0 + b * BT_THREADS;
+                    if (e < nq) {
+                        const int i = e / wq, q = e - i * wq;
+                        const uint32_t v4[4] = {v[b].x, v[b].y, v[b].z, v[b].w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int t = 4 * q + u < w ? sm.colt[4 * q + u] : -1;
+                            if (t >= 0) Ft[t * ldF + i] = to_balanced(v4[u], f);
+                        }
+                    }
                 }
             }
         }
@@ -612,26 +664,34 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             }
             // update: rows in [r, r+k) receive R, every other row A -= F R
             // (MR rows x 4 columns per work item; MR = 8 for 64-column panels,
-            // whose blocks own an SM alone, 4 otherwise so two blocks fit)
+            // whose blocks own an SM alone, 4 otherwise).  The item's
+            // current values are prefetched before the products when the
+            // registers allow (PREF), else read four rows at a time after the
+            // products (loads cannot pass the item's earlier stores to the
+            // same matrix), where the other warps' products hide their latency.
             constexpr int MR = NB >= 64 ? 8 : 4;
+            constexpr bool PREF = MR == 4 || NB >= 64;
             const int rgroups = (m + MR - 1) / MR;
             constexpr int cq = BT_TB / 4;
             for (int e = tid; e < rgroups * cq; e += BT_THREADS) {
                 const int d0 = (e / cq) * MR, jq = (e % cq) * 4;
                 if (jq >= tw) continue;
-                // prefetch the item's current values so their latency overlaps the products
-                uint4 cur[MR];
-#pragma unroll
-                for (int a = 0; a < MR; ++a) {
-                    const int d = d0 + a;
+                auto load_cur = [&](int d) {
+                    uint4 c = make_uint4(0u, 0u, 0u, 0u);
                     const uint32_t* rowp = A + (int64_t)d * ld + j0 + jq;
-                    if (d < m && jq + 4 <= tw && vec_ok) cur[a] = *reinterpret_cast<const uint4*>(rowp);
+                    if (d < m && jq + 4 <= tw && vec_ok) c = *reinterpret_cast<const uint4*>(rowp);
                     else if (d < m) {
-                        cur[a].x = rowp[0];
-                        cur[a].y = jq + 1 < tw ? rowp[1] : 0u;
-                        cur[a].z = jq + 2 < tw ? rowp[2] : 0u;
-                        cur[a].w = jq + 3 < tw ? rowp[3] : 0u;
-                    } else cur[a] = make_uint4(0u, 0u, 0u, 0u);
+                        c.x = rowp[0];
+                        c.y = jq + 1 < tw ? rowp[1] : 0u;
+                        c.z = jq + 2 < tw ? rowp[2] : 0u;
+                        c.w = jq + 3 < tw ? rowp[3] : 0u;
+                    }
+                    return c;
+                };
+                uint4 cur[MR];
+                if (PREF) {
+#pragma unroll
+                    for (int a = 0; a < MR; ++a) cur[a] = load_cur(d0 + a);
                 }
                 int64_t acc[MR][4];
 #pragma unroll
@@ -663,6 +723,12 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
                 }
 #pragma unroll
                 for (int a = 0; a < MR; ++a) {
+                    // without the prefetch, the current values of four rows
+                    // at a time are read before their stores
+                    if (!PREF && (a & 3) == 0) {
+#pragma unroll
+                        for (int a2 = 0; a2 < 4; ++a2) cur[a + a2] = load_cur(d0 + a + a2);
+                    }
                     const int d = d0 + a;
                     if (d >= m) continue;
                     uint32_t* row = A + (int64_t)d * ld + j0;
