@@ -349,6 +349,49 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
     return k;
 }
 
+// The K loop of a tile product: acc[a][b] += X[t][a] * Y[t][b] for t < k,
+// with X rows of MR values (stride ldx) and Y rows of 4 values (stride ldy),
+// all balanced residues (YBAL: Y holds raw residues, balanced on the fly).
+// The loop is unrolled by the fold cadence FOLD, so the folds sit at fixed
+// places and the shared-memory reads of a group issue together; the last
+// k mod FOLD products need no fold before the final reduction (fewer than
+// FOLD products after a fold keep the accumulator bound).
+template <int FOLD, int MR, int SH, bool YBAL>
+__device__ __forceinline__ void bt_kloop(int64_t (&acc)[MR][4], const int32_t* __restrict__ X, int ldx,
+                                         const int32_t* __restrict__ Y, int ldy, int k, const Field& f,
+                                         const FoldShifts& fs) {
+    static_assert(MR == 4 || MR == 8, "four or eight rows per item");
+    auto step = [&](int t) {
+        int xa[MR];
+        const int4 x0 = *reinterpret_cast<const int4*>(X + t * ldx);
+        xa[0] = x0.x; xa[1] = x0.y; xa[2] = x0.z; xa[3] = x0.w;
+        if (MR == 8) {
+            const int4 x1 = *reinterpret_cast<const int4*>(X + t * ldx + 4);
+            xa[MR - 4] = x1.x; xa[MR - 3] = x1.y; xa[MR - 2] = x1.z; xa[MR - 1] = x1.w;
+        }
+        const int4 yv = *reinterpret_cast<const int4*>(Y + t * ldy);
+        int yb[4] = {yv.x, yv.y, yv.z, yv.w};
+        if (YBAL) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) yb[b] = to_balanced((uint32_t)yb[b], f);
+        }
+#pragma unroll
+        for (int a = 0; a < MR; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += (int64_t)xa[a] * yb[b];
+    };
+    const int kf = k - k % FOLD;
+    for (int t0 = 0; t0 < kf; t0 += FOLD) {
+#pragma unroll
+        for (int tt = 0; tt < FOLD; ++tt) step(t0 + tt);
+#pragma unroll
+        for (int a = 0; a < MR; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fold_any<SH>(acc[a][b], f, fs);
+    }
+    for (int t = kf; t < k; ++t) step(t);
+}
+
 // Reduce system A (m x n, leading dimension ld) in place.  mode 0: pivot
 // search; mode 1: reuse the probe's pattern (pat_J / pat_Pi / pat_k per
 // panel) and report failure (returns false) when a reused pivot vanishes or
@@ -628,23 +671,10 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
                     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-                for (int s2 = 0; s2 < kp; ++s2) {
-                    const int4 ev = *reinterpret_cast<const int4*>(Et + s2 * NB + t0);
-                    const uint4 vv = *reinterpret_cast<const uint4*>(Vcur + s2 * BT_TB + jq);
-                    const int ea[4] = {ev.x, ev.y, ev.z, ev.w};
-                    const int vb[4] = {to_balanced(vv.x, f), to_balanced(vv.y, f), to_balanced(vv.z, f),
-                                       to_balanced(vv.w, f)};
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] += (int64_t)ea[a] * vb[b];
-                    if ((s2 & fo.mask) == fo.mask) {
-#pragma unroll
-                        for (int a = 0; a < 4; ++a)
-#pragma unroll
-                            for (int b = 0; b < 4; ++b) acc[a][b] = fold_any<SH>(acc[a][b], f, fo.fs);
-                    }
-                }
+                if (fo.mask == 7)
+                    bt_kloop<8, 4, SH, true>(acc, Et + t0, NB, (const int32_t*)Vcur + jq, BT_TB, kp, f, fo.fs);
+                else
+                    bt_kloop<4, 4, SH, true>(acc, Et + t0, NB, (const int32_t*)Vcur + jq, BT_TB, kp, f, fo.fs);
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -698,29 +728,10 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
                 for (int a = 0; a < MR; ++a)
 #pragma unroll
                     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-                for (int t = 0; t < k; ++t) {
-                    int fa[MR];
-                    {
-                        const int4 f0 = *reinterpret_cast<const int4*>(Ft + t * ldF + d0);
-                        fa[0] = f0.x; fa[1] = f0.y; fa[2] = f0.z; fa[3] = f0.w;
-                        if (MR == 8) {
-                            const int4 f1 = *reinterpret_cast<const int4*>(Ft + t * ldF + d0 + (MR - 4));
-                            fa[MR - 4] = f1.x; fa[MR - 3] = f1.y; fa[MR - 2] = f1.z; fa[MR - 1] = f1.w;
-                        }
-                    }
-                    const int4 rv = *reinterpret_cast<const int4*>(Rt + t * BT_TB + jq);
-                    const int rb[4] = {rv.x, rv.y, rv.z, rv.w};
-#pragma unroll
-                    for (int a = 0; a < MR; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] += (int64_t)fa[a] * rb[b];
-                    if ((t & fo.mask) == fo.mask) {
-#pragma unroll
-                        for (int a = 0; a < MR; ++a)
-#pragma unroll
-                            for (int b = 0; b < 4; ++b) acc[a][b] = fold_any<SH>(acc[a][b], f, fo.fs);
-                    }
-                }
+                if (fo.mask == 7)
+                    bt_kloop<8, MR, SH, false>(acc, Ft + d0, ldF, Rt + jq, BT_TB, k, f, fo.fs);
+                else
+                    bt_kloop<4, MR, SH, false>(acc, Ft + d0, ldF, Rt + jq, BT_TB, k, f, fo.fs);
 #pragma unroll
                 for (int a = 0; a < MR; ++a) {
                     // without the prefetch, the current values of four rows
