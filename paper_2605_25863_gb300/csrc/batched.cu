@@ -939,17 +939,21 @@ int g_bt_nb[64][BT_NBUCKETS];   // 0 = default
 static int bt_default_nb(int b) { (void)b; return 32; }
 
 // The shift form is used only when 2^32 mod p is a single power of two
-// (2^31 - 1): with two or three shifts the fold and the reduction issue more
-// ALU instructions than the multiply-pipe forms they replace, and this kernel
-// is bound by issue and latency rather than by the multiply pipe.
+// (2^31 - 1): with two or three shifts the fold issues more ALU instructions
+// than the multiply-pipe form it replaces, and this kernel is bound by issue
+// and latency rather than by the multiply pipe.  The final reduction takes
+// two folds and two conditional subtractions (reduce_alu) whenever
+// c32 = 2^32 mod p is small enough, whatever its bit count (2^31 - 19:
+// c32 = 38), and the Barrett reduction otherwise.
 static BtFold bt_fold_params(const Field& f) {
     BtFold fo;
     fo.mask = f.fold >= 8 ? 7 : 3;
     fo.nshift = fold_shifts(f, &fo.fs);
-    if (fo.nshift != 1) {
-        fo.nshift = 0;
-        fo.fs.alu_reduce = 0;
-    }
+    if (fo.nshift != 1) fo.nshift = 0;
+    const unsigned __int128 cc = f.c32;
+    const bool low_ok = cc * (cc + 1) / 2 <= f.p;
+    const bool high_ok = (((unsigned __int128)1) << 32) - 1 + cc * (cc / 2 + 1) < (unsigned __int128)3 * f.p;
+    fo.fs.alu_reduce = low_ok && high_ok;
     return fo;
 }
 

@@ -145,8 +145,10 @@ __device__ __forceinline__ int64_t fold_any(int64_t acc, const Field& f, const F
     return out;
 }
 
-// Canonical residue of a signed 64-bit accumulator (|acc| < 2^63) without
-// multiplies, for SHIFTS > 0 and fs.alu_reduce.  Two folds bring acc to
+// Canonical residue of a signed 64-bit accumulator (|acc| < 2^63) by two
+// folds and two conditional subtractions, whenever fs.alu_reduce (without
+// any multiply when SHIFTS > 0; SHIFTS = 0 folds on the multiply pipe, which
+// computes the same L + sext(H) c32).  Two folds bring acc to
 //   t2 = L2 + H2*c32 with H2 in [-(c32+1)/2, c32/2 + 1], so
 //   t2 in [-c32 (c32+1)/2, 2^32 - 1 + c32 (c32/2 + 1)];
 // the host sets alu_reduce only when c32 (c32+1)/2 <= p and
@@ -166,7 +168,7 @@ __device__ __forceinline__ uint32_t reduce_alu(int64_t acc, const Field& f, cons
 // applies, the Barrett reduction otherwise.
 template <int SHIFTS>
 __device__ __forceinline__ uint32_t reduce_acc(int64_t acc, const Field& f, const FoldShifts& fs) {
-    if (SHIFTS > 0 && fs.alu_reduce) return reduce_alu<(SHIFTS > 0 ? SHIFTS : 1)>(acc, f, fs);
+    if (fs.alu_reduce) return reduce_alu<SHIFTS>(acc, f, fs);
     return reduce_signed(acc, f);
 }
 

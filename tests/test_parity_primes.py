@@ -21,6 +21,19 @@ the oracle, at primes that take the other branches:
                          shift fold, but the multiply-free reduction's
                          bounds fail (c32 (c32 + 1)/2 > p), so Barrett
 
+The batched kernel (its own fold and reduction choices) is also run at
+
+  P_EDGE_IN  2147450923  2^32 mod p = 65450 (12 set bits): the largest such
+                         value below 2^16 whose two-fold reduction bounds
+                         (c32 (c32 + 1)/2 <= p, 2^32 - 1 + c32 (c32/2 + 1) < 3p)
+                         still hold, so the batched kernel folds on the
+                         multiply pipe and reduces by two folds and two
+                         conditional subtractions; fold every 8 products
+  P_EDGE_OUT 2147450861  2^32 mod p = 65574: just outside those bounds, so
+                         Barrett; fold every 8
+  2^31 - 19              2^32 mod p = 38: multiply-pipe fold every 8 with the
+                         two-fold reduction
+
 The CPU test at the end checks those properties of the primes themselves.
 Shapes span two or more panels with ragged tails, at panel widths 128 and 32;
 one matrix has entries (p - 1)/2 and (p + 1)/2 only, the balanced
@@ -44,6 +57,9 @@ P_DENSE31 = 1908903247
 P_DENSE16 = 1381576943
 P_SPARSE = 2147418079
 DENSE_PRIMES = [P_BIGFOLD, P_DENSE31, P_DENSE16, 251, P_SPARSE]
+P_EDGE_IN = 2147450923
+P_EDGE_OUT = 2147450861
+BATCHED_PRIMES = DENSE_PRIMES + [P_EDGE_IN, P_EDGE_OUT, 2**31 - 19]
 
 
 def _is_prime(n):
@@ -81,6 +97,13 @@ def test_primes_take_the_dense_fold_branches():
     for p in (2**31 - 1, 2**31 - 19):
         c = (1 << 32) % p
         assert bin(c).count("1") <= 3 and c * (c + 1) // 2 <= p
+    # the edge primes of the two-fold reduction's bounds
+    two_fold = lambda p, c: c * (c + 1) // 2 <= p and (1 << 32) - 1 + c * (c // 2 + 1) < 3 * p
+    for p, inside in ((P_EDGE_IN, True), (P_EDGE_OUT, False)):
+        c = (1 << 32) % p
+        assert _is_prime(p) and p < 2**31 and bin(c).count("1") > 3 and _fold_cadence(p) == 8
+        assert two_fold(p, c) == inside
+    assert _fold_cadence(2**31 - 19) == 8 and two_fold(2**31 - 19, 38)
 
 
 def _gpu_rref(M, p, **kw):
@@ -157,7 +180,7 @@ def test_solve_vs_oracle_dense_fold(p):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("p", DENSE_PRIMES)
+@pytest.mark.parametrize("p", BATCHED_PRIMES)
 def test_batched_vs_oracle_dense_fold(p):
     """linac_rref_batched (its own Montgomery and fold arithmetic) at the same
     primes, systems in every size bucket."""
@@ -171,6 +194,13 @@ def test_batched_vs_oracle_dense_fold(p):
             S[m - 3:] = matmul_mod(g.integers(0, p, size=(3, m - 3), dtype=np.int64).astype(np.uint32),
                                    S[:m - 3], p)
         systems.append(S)
+    _batched_check(systems, p)
+
+
+def _batched_check(systems, p):
+    """linac_rref_batched on the systems (4 right-hand-side columns outside the
+    search where the system has more than 4 columns), every system compared
+    with the oracle element by element."""
     B = synth._pack(systems, p, [s.shape[1] - 4 if s.shape[1] > 4 else s.shape[1] for s in systems],
                     [0] * len(systems))
     dev = torch.device("cuda")
@@ -187,3 +217,16 @@ def test_batched_vs_oracle_dense_fold(p):
         assert ranks[s] == r0, f"system {s}"
         assert np.array_equal(piv[poff[s]:poff[s] + r0], piv0), f"system {s}"
         assert np.array_equal(out[o:o + m * ld].reshape(m, ld)[:, :n], R0), f"system {s}"
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("p", [P_EDGE_IN, P_EDGE_OUT, 2**31 - 19])
+def test_batched_balanced_extremes(p):
+    """Entries (p - 1)/2 and (p + 1)/2 only, so the first panel's products sit
+    at the accumulator bound, in systems of every size bucket, through the
+    batched kernel's fold and its two-fold or Barrett reduction."""
+    g = np.random.default_rng(p % 6007)
+    half = (p - 1) // 2
+    shapes = [(40, 44), (100, 104), (200, 204), (300, 304), (511, 515), (700, 704)]
+    systems = [np.where(g.integers(0, 2, size=sh) == 1, half, half + 1).astype(np.uint32) for sh in shapes]
+    _batched_check(systems, p)
