@@ -148,20 +148,32 @@ __device__ __forceinline__ int block_min(int v, BtSmall<NB>& sm) {
     return sm.s_min;
 }
 
-// Block-wide minimum with one barrier: each warp posts its minimum in one of
-// two alternating slots and every thread reduces the posts itself.  A slot is
-// written again two calls later, after another barrier, when every thread has
-// read it.
-template <int NB>
+// Barrier of the first WT threads of the block: the whole block's barrier,
+// or named barrier 1 when fewer threads take part.
+template <int WT>
+__device__ __forceinline__ void bt_wsync() {
+    if (WT == BT_THREADS) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"n"(WT) : "memory");
+}
+
+// Minimum over the first WT threads with one barrier: each warp posts its
+// minimum in one of two alternating slots and every thread reduces the posts
+// itself.  A slot is written again two calls later, after another barrier,
+// when every thread has read it.
+template <int NB, int WT = BT_THREADS>
 __device__ __forceinline__ int block_min1(int v, BtSmall<NB>& sm, int& buf) {
-    static_assert(BT_THREADS == 256, "eight warp minima, read as two 16-byte words");
+    static_assert(WT == 256 || WT == 128, "four or eight warp minima, read as 16-byte words");
     v = __reduce_min_sync(0xffffffffu, v);
     if ((threadIdx.x & 31) == 0) sm.red2[buf][threadIdx.x >> 5] = v;
-    __syncthreads();
+    bt_wsync<WT>();
     const int4 a = *reinterpret_cast<const int4*>(&sm.red2[buf][0]);
-    const int4 b = *reinterpret_cast<const int4*>(&sm.red2[buf][4]);
+    int x = min(min(a.x, a.y), min(a.z, a.w));
+    if (WT == 256) {
+        const int4 b = *reinterpret_cast<const int4*>(&sm.red2[buf][4]);
+        x = min(x, min(min(b.x, b.y), min(b.z, b.w)));
+    }
     buf ^= 1;
-    return min(min(min(a.x, a.y), min(a.z, a.w)), min(min(b.x, b.y), min(b.z, b.w)));
+    return x;
 }
 
 // Fold cadence of the lazy accumulators (fold after products t with
@@ -201,40 +213,43 @@ struct BtFold {
 //
 // The w - cc - 1 panel columns and s + 1 <= cc + 1 coefficients that change
 // at column cc fit in NB slab columns, so the block is laid out as NB
-// columns by BT_THREADS / NB row groups, and column slot cp of a thread names
+// columns by WT / NB row groups, and column slot cp of a thread names
 // panel column cc + 1 + cp, or coefficient cp - (w - cc - 1).  A thread keeps
 // the pivot flags of its own rows in one register.
+//
+// Only the first WT threads of the block take part (their own barrier when
+// WT is below the block size).
 //
 // Returns the number of pivots k, or -1 in forced mode when a given pivot
 // vanished.  Unless forced mode, k == w or keep != 0, E is not needed and is
 // not formed; otherwise Et[u * NB + t] = balanced E[t][u] for t, u < k
 // rounded up to 4, zero padded.  Fills sm.J, sm.Pi, sm.own (search) and
 // sm.hs[t] = H_t (held form).
-template <int NB>
+template <int NB, int WT = BT_THREADS>
 __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int64_t ld, int r, int c0, int w, int rows,
                             int forced, int keep, const Field& f, uint32_t* __restrict__ G,
                             BtSmall<NB>& sm, int32_t* __restrict__ Et) {
     constexpr int SWG = 2 * NB + 1;
     constexpr int CW = NB;                  // column slots
-    constexpr int RGN = BT_THREADS / CW;    // row groups
+    constexpr int RGN = WT / CW;            // row groups
     constexpr int UMAX = (bt_win_rows(NB) + RGN - 1) / RGN;
-    constexpr int U = UMAX < 6 ? UMAX : 6;  // rows per batch of independent updates
-    static_assert(BT_THREADS % CW == 0, "column slots must divide the block");
+    constexpr int U = UMAX <= 10 ? UMAX : 6;   // rows per batch of independent updates
+    static_assert(WT % CW == 0, "column slots must divide the block");
     static_assert(UMAX <= 32, "the pivot flags of a thread's rows fit one word");
     const int tid = threadIdx.x;
     const int cp = tid % CW, rg = tid / CW;
     // load: the panel entries in Montgomery form, coefficients zero; up to 8
     // loads of a thread in flight at once
-    constexpr int LPT = (bt_win_rows(NB) * NB + BT_THREADS - 1) / BT_THREADS;
+    constexpr int LPT = (bt_win_rows(NB) * NB + WT - 1) / WT;
     constexpr int LB = LPT < 8 ? LPT : 8;
     const int nload = rows * NB;
     int cand = INT_MAX;
-    for (int e = tid; e < nload; e += BT_THREADS) G[(e / NB) * SWG + NB + e % NB] = 0u;
-    for (int e0 = 0; e0 < nload; e0 += LB * BT_THREADS) {
+    for (int e = tid; e < nload; e += WT) G[(e / NB) * SWG + NB + e % NB] = 0u;
+    for (int e0 = 0; e0 < nload; e0 += LB * WT) {
         uint32_t v[LB];
 #pragma unroll
         for (int b = 0; b < LB; ++b) {
-            const int e = e0 + b * BT_THREADS + tid;
+            const int e = e0 + b * WT + tid;
             v[b] = 0u;
             if (e < nload) {
                 const int i = e / NB, c = e % NB;
@@ -244,7 +259,7 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
         }
 #pragma unroll
         for (int b = 0; b < LB; ++b) {
-            const int e = e0 + b * BT_THREADS + tid;
+            const int e = e0 + b * WT + tid;
             if (e < nload) {
                 const int i = e / NB, c = e % NB;
                 G[i * SWG + c] = to_mont(v[b], f);
@@ -254,8 +269,8 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
     }
     int buf = 0;
     int q = INT_MAX;
-    if (forced) __syncthreads();
-    else q = block_min1<NB>(cand, sm, buf);   // also the barrier after the load
+    if (forced) bt_wsync<WT>();
+    else q = block_min1<NB, WT>(cand, sm, buf);   // also the barrier after the load
     uint32_t Hs = f.c32;   // H_0 = 1, held form R mod p
     uint32_t pmask = 0;    // bit j: window row rg + j RGN is a pivot row
     int s = 0;
@@ -288,13 +303,18 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
                     fi[u] = (i < rows && act) ? G[i * SWG + cc] : 0u;
                     x[u] = i < rows ? G[i * SWG + col] : 0u;
                 }
+                // the products of every row first, unconditionally, so the
+                // rows' dependent chains interleave; only the stores and the
+                // kept values depend on the row
+                uint32_t xn[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) xn[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int i = i0 + u * RGN;
-                    if (act && i < rows && i != qq) {
-                        x[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
-                        G[i * SWG + col] = x[u];
-                    }
+                    const bool upd = act && i < rows && i != qq;
+                    if (upd) G[i * SWG + col] = xn[u];
+                    x[u] = upd ? xn[u] : x[u];
                 }
                 if (cand_col) {
 #pragma unroll
@@ -322,8 +342,8 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
         // same in every thread, so the whole block returns; a pivot found by
         // the search is nonzero)
         if (forced && h == 0u) return -1;
-        if (!forced && cc + 1 < w) q = block_min1<NB>(cand, sm, buf);
-        else __syncthreads();
+        if (!forced && cc + 1 < w) q = block_min1<NB, WT>(cand, sm, buf);
+        else bt_wsync<WT>();
     }
     const int k = s;
     if (!forced && k < w && !keep) return k;
@@ -333,10 +353,10 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
         const uint32_t inv = inverse_fermat(Hs, f);
         if (tid == 0) sm.s_inv = inv;
     }
-    __syncthreads();
+    bt_wsync<WT>();
     const uint32_t invH = sm.s_inv;
     const int kp = (k + 3) & ~3;
-    for (int e = tid; e < kp * kp; e += BT_THREADS) {
+    for (int e = tid; e < kp * kp; e += WT) {
         const int u = e / kp, t = e % kp;
         int32_t v = 0;
         if (t < k && u < k) {
@@ -345,7 +365,7 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
         }
         Et[u * NB + t] = v;
     }
-    __syncthreads();
+    bt_wsync<WT>();
     return k;
 }
 
@@ -360,11 +380,16 @@ template <int FOLD, int MR, int SH, bool YBAL>
 __device__ __forceinline__ void bt_kloop(int64_t (&acc)[MR][4], const int32_t* __restrict__ X, int ldx,
                                          const int32_t* __restrict__ Y, int ldy, int k, const Field& f,
                                          const FoldShifts& fs) {
-    static_assert(MR == 4 || MR == 8, "four or eight rows per item");
+    static_assert(MR == 2 || MR == 4 || MR == 8, "two, four or eight rows per item");
     auto step = [&](int t) {
         int xa[MR];
-        const int4 x0 = *reinterpret_cast<const int4*>(X + t * ldx);
-        xa[0] = x0.x; xa[1] = x0.y; xa[2] = x0.z; xa[3] = x0.w;
+        if (MR == 2) {
+            const int2 x0 = *reinterpret_cast<const int2*>(X + t * ldx);
+            xa[0] = x0.x; xa[MR - 1] = x0.y;
+        } else {
+            const int4 x0 = *reinterpret_cast<const int4*>(X + t * ldx);
+            xa[0] = x0.x; xa[1 % MR] = x0.y; xa[2 % MR] = x0.z; xa[3 % MR] = x0.w;
+        }
         if (MR == 8) {
             const int4 x1 = *reinterpret_cast<const int4*>(X + t * ldx + 4);
             xa[MR - 4] = x1.x; xa[MR - 3] = x1.y; xa[MR - 2] = x1.z; xa[MR - 1] = x1.w;
@@ -565,18 +590,36 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             }
             for (int e = tid; e < k * k; e += BT_THREADS) E[(e / k) * NB + (e % k)] = (e / k == e % k) ? 1u : 0u;
         }
-        if (tid == 0) {
-            // move plan: rows of [r, r+k) without a pivot go to the pivot rows' old places
-            unsigned char occ[NB];
-            for (int d = 0; d < k; ++d) occ[d] = 0;
-            for (int t = 0; t < k; ++t)
-                if (sm.Pi[t] >= r && sm.Pi[t] < r + k) occ[sm.Pi[t] - r] = 1;
-            int a = 0, b = 0;
-            for (int d = 0; d < k; ++d)
-                if (!occ[d]) sm.srcs[a++] = r + d;
-            for (int t = 0; t < k; ++t)
-                if (sm.Pi[t] < r || sm.Pi[t] >= r + k) sm.dsts[b++] = sm.Pi[t];
-            sm.s_npairs = a;
+        if (tid < 32) {
+            // move plan (warp 0): the rows of [r, r+k) without a pivot, in
+            // order, go to the pivot rows' old places outside [r, r+k), in
+            // pivot order (k <= NB <= 64: one 64-bit occupancy mask)
+            static_assert(NB <= 64, "occupancy of [r, r+k) in one 64-bit mask");
+            const unsigned full = 0xffffffffu;
+            unsigned long long occ = 0;
+            for (int t = tid; t < k; t += 32) {
+                const int d = sm.Pi[t] - r;
+                if (d >= 0 && d < k) occ |= 1ull << d;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) occ |= __shfl_xor_sync(full, occ, o);
+            const unsigned below = (1u << tid) - 1u;
+            int na = 0, nb2 = 0;
+            for (int d0 = 0; d0 < k; d0 += 32) {
+                const int d = d0 + tid;
+                const bool freed = d < k && !((occ >> d) & 1ull);
+                const unsigned bal = __ballot_sync(full, freed);
+                if (freed) sm.srcs[na + __popc(bal & below)] = r + d;
+                na += __popc(bal);
+            }
+            for (int t0 = 0; t0 < k; t0 += 32) {
+                const int t = t0 + tid;
+                const bool out = t < k && (sm.Pi[t] < r || sm.Pi[t] >= r + k);
+                const unsigned bal = __ballot_sync(full, out);
+                if (out) sm.dsts[nb2 + __popc(bal & below)] = sm.Pi[t];
+                nb2 += __popc(bal);
+            }
+            if (tid == 0) sm.s_npairs = na;
         }
         __syncthreads();
         if (!e_ready) {
@@ -663,20 +706,21 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             }
             cp_async_wait<0>();
             __syncthreads();
-            // R = E V, 4 x 4 outputs per thread (balanced operands, lazy signed accumulation)
-            for (int e = tid; e < (kp / 4) * (BT_TB / 4); e += BT_THREADS) {
-                const int t0 = (e / (BT_TB / 4)) * 4, jq = (e % (BT_TB / 4)) * 4;
-                int64_t acc[4][4];
+            // R = E V, 2 x 4 outputs per thread (balanced operands, lazy
+            // signed accumulation): k/2 x 16 items keep every thread busy
+            for (int e = tid; e < (kp / 2) * (BT_TB / 4); e += BT_THREADS) {
+                const int t0 = (e / (BT_TB / 4)) * 2, jq = (e % (BT_TB / 4)) * 4;
+                int64_t acc[2][4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 2; ++a)
 #pragma unroll
                     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
                 if (fo.mask == 7)
-                    bt_kloop<8, 4, SH, true>(acc, Et + t0, NB, (const int32_t*)Vcur + jq, BT_TB, kp, f, fo.fs);
+                    bt_kloop<8, 2, SH, true>(acc, Et + t0, NB, (const int32_t*)Vcur + jq, BT_TB, kp, f, fo.fs);
                 else
-                    bt_kloop<4, 4, SH, true>(acc, Et + t0, NB, (const int32_t*)Vcur + jq, BT_TB, kp, f, fo.fs);
+                    bt_kloop<4, 2, SH, true>(acc, Et + t0, NB, (const int32_t*)Vcur + jq, BT_TB, kp, f, fo.fs);
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 2; ++a)
 #pragma unroll
                     for (int b = 0; b < 4; ++b) Rt[(t0 + a) * BT_TB + jq + b] = to_balanced(reduce_acc<SH>(acc[a][b], f, fo.fs), f);
             }
