@@ -39,12 +39,17 @@ __host__ __device__ constexpr int bt_bucket_max(int b) { return 64 << b; }
 constexpr int BT_FLAG_FALLBACK = 0x100;
 constexpr int BT_WINDOW = 8;          // rows of the pivot window beyond the panel width
 
-// The pivot window's slab: bt_win_rows rows of 2 NB + 1 words (NB panel
+// The pivot window's slab: bt_win_rows_pad rows of 2 NB + 1 words (NB panel
 // entries, NB coefficients over the pivot rows, one pad word against bank
 // conflicts).
 __host__ __device__ constexpr int bt_win_rows(int nb) { return nb + BT_WINDOW; }
+// rows of the slab: bt_win_rows rounded up to whole batches of the block's
+// BT_THREADS / nb row groups (the rows beyond the window hold zeros)
+__host__ __device__ constexpr int bt_win_rows_pad(int nb) {
+    return (bt_win_rows(nb) + BT_THREADS / nb - 1) / (BT_THREADS / nb) * (BT_THREADS / nb);
+}
 __host__ __device__ constexpr size_t bt_win_bytes(int nb) {
-    return (size_t)bt_win_rows(nb) * (2 * nb + 1) * 4;
+    return (size_t)bt_win_rows_pad(nb) * (2 * nb + 1) * 4;
 }
 
 // Per-call device scratch of the batched driver.
@@ -242,9 +247,15 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
     // loads of a thread in flight at once
     constexpr int LPT = (bt_win_rows(NB) * NB + WT - 1) / WT;
     constexpr int LB = LPT < 8 ? LPT : 8;
+    constexpr int PR = RGN * UMAX;   // slab rows: the rows beyond `rows` hold zeros and stay zero
+    static_assert((size_t)PR * SWG * 4 <= bt_win_bytes(NB), "the padded slab fits its region");
     const int nload = rows * NB;
     int cand = INT_MAX;
-    for (int e = tid; e < nload; e += WT) G[(e / NB) * SWG + NB + e % NB] = 0u;
+    for (int e = tid; e < PR * NB; e += WT) {
+        const int i = e / NB, c = e % NB;
+        G[i * SWG + NB + c] = 0u;
+        if (i >= rows) G[i * SWG + c] = 0u;
+    }
     for (int e0 = 0; e0 < nload; e0 += LB * WT) {
         uint32_t v[LB];
 #pragma unroll
@@ -295,38 +306,43 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
         const bool cand_col = !forced && cp == 0 && np > 0;   // col == cc + 1
         cand = INT_MAX;
         if (act || cand_col) {
-            for (int i0 = rg, j0 = 0; i0 < rows; i0 += U * RGN, j0 += U) {
+            // every row of the padded slab is computed with no row tests
+            // (zero padding rows stay zero and never offer a candidate); the
+            // pivot row's owner does not store its row, which the other
+            // threads read as pv during this step, and sets its coefficient
+            // a_ss = H_s instead
+            const int uq = (has && qq % RGN == rg) ? qq / RGN : -1;
+#pragma unroll
+            for (int b0 = 0; b0 < UMAX; b0 += U) {
                 uint32_t x[U], fi[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int i = i0 + u * RGN;
-                    fi[u] = (i < rows && act) ? G[i * SWG + cc] : 0u;
-                    x[u] = i < rows ? G[i * SWG + col] : 0u;
+                    const int i = rg + (b0 + u) * RGN;
+                    fi[u] = (b0 + u < UMAX && act) ? G[i * SWG + cc] : 0u;
+                    x[u] = b0 + u < UMAX ? G[i * SWG + col] : 0u;
                 }
-                // the products of every row first, unconditionally, so the
-                // rows' dependent chains interleave; only the stores and the
-                // kept values depend on the row
-                uint32_t xn[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) xn[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int i = i0 + u * RGN;
-                    const bool upd = act && i < rows && i != qq;
-                    if (upd) G[i * SWG + col] = xn[u];
-                    x[u] = upd ? xn[u] : x[u];
-                }
-                if (cand_col) {
+                if (act) {
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const int i = i0 + u * RGN;
-                        if (i < rows && x[u] != 0u && !((pmask >> (j0 + u)) & 1u) && i < cand) cand = i;
+                        if (b0 + u < UMAX) {
+                            x[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
+                            if (b0 + u != uq) G[(rg + (b0 + u) * RGN) * SWG + col] = x[u];
+                        }
                     }
                 }
+                if (cand_col) {
+                    // the lowest row of this thread that is nonzero in column
+                    // cc + 1 and not yet a pivot row
+                    uint32_t nz = 0u;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) nz |= (b0 + u < UMAX && x[u] != 0u) ? (1u << (b0 + u)) : 0u;
+                    nz &= ~pmask;
+                    if (nz != 0u && cand == INT_MAX) cand = rg + (__ffs((int)nz) - 1) * RGN;
+                }
             }
+            if (col_s && uq >= 0) G[qq * SWG + col] = Hs;
         }
         if (has) {
-            if (col_s && qq % RGN == rg) G[qq * SWG + col] = Hs;
             if (tid == 0) {
                 sm.hs[s] = Hs;
                 if (!forced) {
