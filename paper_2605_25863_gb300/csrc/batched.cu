@@ -553,13 +553,43 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             if (bt_window_gj<NB>(A, ld, r, c0, w, k, 1, 1, f, P, sm, Et) < 0) return false;
         }
         if (k == 0) continue;
+        // kp = k rounded up to 4 (E^T and the tiles are zero padded to it)
+        const int kp = (k + 3) & ~3;
+        // the pivot rows' first column tile V (raw residues), copied with
+        // cp.async now, so it lands during the F load; later tiles are copied
+        // one tile ahead, during the previous tile's update (which writes only
+        // its own tile's columns, so the next tile of the pivot rows is final).
+        // Without 16-byte row alignment the copy is synchronous.  The window
+        // slab, which the tiles may overlap, is dead here.
+        uint32_t* Vcur = V;
+        uint32_t* Vnxt = Vnext;
+        auto fetch_v = [&](int j0v, uint32_t* dst) {
+            const int twv = min(BT_TB, n - j0v);
+            if (vec_ok) {
+                for (int e = tid; e < kp * (BT_TB / 4); e += BT_THREADS) {
+                    const int t = e / (BT_TB / 4), j = (e % (BT_TB / 4)) * 4;
+                    const int bytes = (t < k && j < twv) ? min(4, twv - j) * 4 : 0;
+                    const uint32_t* src = bytes ? A + (int64_t)sm.Pi[t] * ld + j0v + j : A;
+                    cp_async16(dst + t * BT_TB + j, src, bytes);
+                }
+                cp_async_commit();
+            } else {
+                for (int e = tid; e < kp * BT_TB; e += BT_THREADS) {
+                    const int t = e / BT_TB, j = e % BT_TB;
+                    dst[t * BT_TB + j] = (t < k && j < twv) ? A[(int64_t)sm.Pi[t] * ld + j0v + j] : 0u;
+                }
+            }
+        };
+        fetch_v(c0, Vcur);
         // multipliers F (original entries at the pivot columns, all of which lie
         // in the panel's w columns): each row's panel segment is read as
         // 16-byte words, coalesced, and every entry of a pivot column is
         // written to F through the column -> pivot map colt
-        for (int j = tid; j < NB; j += BT_THREADS) sm.colt[j] = -1;
-        __syncthreads();
-        for (int t = tid; t < k; t += BT_THREADS) sm.colt[sm.J[t] - c0] = t;
+        if (tid < 32) {
+            for (int j = tid; j < NB; j += 32) sm.colt[j] = -1;
+            __syncwarp();
+            for (int t = tid; t < k; t += 32) sm.colt[sm.J[t] - c0] = t;
+        }
         __syncthreads();
         {
             const int wq = (w + 3) >> 2;
@@ -670,9 +700,8 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             const int t = e / npairs, a = e % npairs;
             Ft[t * ldF + sm.dsts[a]] = Ft[t * ldF + sm.srcs[a]];
         }
-        // E^T in balanced form (register-tiled R = E V reads 4 consecutive t);
-        // kp = k rounded up to 4, with zero padding
-        const int kp = (k + 3) & ~3;
+        // E^T in balanced form (register-tiled R = E V reads 4 consecutive t),
+        // zero padded to kp
         if (!e_ready) {
             // transpose through registers: each thread owns whole (t, s) entries
             uint32_t v[NB * NB / BT_THREADS + 1];
@@ -688,32 +717,8 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
                 Et[s2 * NB + t] = (int32_t)v[cnt];
             }
         }
-        __syncthreads();
-        // column tiles.  The pivot rows' tile V (raw residues) is copied with
-        // cp.async one tile ahead, during the previous tile's update: the
-        // update writes only its own tile's columns, so the next tile of the
-        // pivot rows is already final.  Without 16-byte row alignment the
-        // copy is synchronous.
-        uint32_t* Vcur = V;
-        uint32_t* Vnxt = Vnext;
-        auto fetch_v = [&](int j0v, uint32_t* dst) {
-            const int twv = min(BT_TB, n - j0v);
-            if (vec_ok) {
-                for (int e = tid; e < kp * (BT_TB / 4); e += BT_THREADS) {
-                    const int t = e / (BT_TB / 4), j = (e % (BT_TB / 4)) * 4;
-                    const int bytes = (t < k && j < twv) ? min(4, twv - j) * 4 : 0;
-                    const uint32_t* src = bytes ? A + (int64_t)sm.Pi[t] * ld + j0v + j : A;
-                    cp_async16(dst + t * BT_TB + j, src, bytes);
-                }
-                cp_async_commit();
-            } else {
-                for (int e = tid; e < kp * BT_TB; e += BT_THREADS) {
-                    const int t = e / BT_TB, j = e % BT_TB;
-                    dst[t * BT_TB + j] = (t < k && j < twv) ? A[(int64_t)sm.Pi[t] * ld + j0v + j] : 0u;
-                }
-            }
-        };
-        fetch_v(c0, Vcur);
+        // column tiles (the first barrier of the tile loop also orders the F
+        // moves and E^T above before anything reads them)
         for (int j0 = c0; j0 < n; j0 += BT_TB) {
             const int tw = min(BT_TB, n - j0);
             for (int e = tid; e < npairs * tw; e += BT_THREADS) {
