@@ -240,11 +240,16 @@ __global__ void __launch_bounds__(WIN1_THREADS)
 window1_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f, DenseState* st,
                uint32_t* __restrict__ panelU, int G, const int32_t* __restrict__ rowmap) {
     constexpr int ROWS = WIN1_NB + WIN_EXTRA, SW = WIN1_NB + 1;
-    __shared__ __align__(16) uint32_t P[ROWS * SW];
+    // thread layout of the elimination: column slot js (column cc + 1 + js)
+    // by row group rg (rows rg, rg + RG1, ...): no division per element
+    constexpr int RG1 = WIN1_THREADS / WIN1_NB;
+    constexpr int U1 = (ROWS + RG1 - 1) / RG1;
+    static_assert(WIN1_THREADS % WIN1_NB == 0 && U1 <= 32, "window layout");
+    __shared__ __align__(16) uint32_t P[U1 * RG1 * SW];
     __shared__ int red[2][WIN1_THREADS / 32];
-    __shared__ unsigned char isp[ROWS];
     __shared__ int own[WIN1_NB], Jc[WIN1_NB];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int js = tid % WIN1_NB, rg = tid / WIN1_NB;
     const int64_t r = st->r;
     const int64_t left = m - r > 0 ? m - r : 0;
     const int rows = (int)(left < w + WIN_EXTRA ? left : w + WIN_EXTRA);
@@ -259,44 +264,63 @@ window1_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, in
         buf ^= 1;
         return x;
     };
+    // load in Montgomery form; rows beyond the window hold zeros (they are
+    // never updated, because their entries f are zero, and never offer a
+    // candidate)
     int cand = INT_MAX;
-    for (int e = tid; e < rows * w; e += WIN1_THREADS) {
+    for (int e = tid; e < U1 * RG1 * w; e += WIN1_THREADS) {
         const int i = e / w, j = e - i * w;
-        const uint32_t v = M[map_row(rowmap, r, i) * ld + c0 + j];
+        const uint32_t v = i < rows ? M[map_row(rowmap, r, i) * ld + c0 + j] : 0u;
         P[i * SW + j] = to_mont(v, f);
         if (j == 0 && v != 0u && i < cand) cand = i;
     }
-    for (int i = tid; i < ROWS; i += WIN1_THREADS) isp[i] = 0;
     int q = block_min(cand);   // also the barrier after the load
     int kk = 0;
+    uint32_t pmask = 0u;       // bit u: row rg + u RG1 is a pivot row
     for (int cc = 0; cc < w; ++cc) {
         if (q != INT_MAX) {
             if (tid == 0) {
-                isp[q] = 1;
                 own[kk] = q;
                 Jc[kk] = cc;
             }
+            if (q % RG1 == rg) pmask |= 1u << (q / RG1);
             ++kk;
         }
         // fraction-free elimination of column cc from the other remaining
-        // rows (row_i <- h row_i - f_i row_q on the columns right of cc), and
-        // the next column's candidate from the updated entries
+        // rows (row_i <- h row_i - f_i row_q on the columns right of cc, for
+        // the rows with f_i != 0, the recurrence einv_kernel replays), and
+        // the next column's candidate from the updated entries.  The products
+        // are computed for every row and kept by a select, so the rows'
+        // dependent chains interleave; only the stores are conditional.
         const int nc = w - cc - 1;
         cand = INT_MAX;
         if (nc > 0) {
-            const uint32_t h = q != INT_MAX ? P[q * SW + cc] : 0u;
-            for (int e = tid; e < rows * nc; e += WIN1_THREADS) {
-                const int i = e / nc, j = cc + 1 + (e - i * nc);
-                if (i == q || isp[i]) continue;
-                uint32_t x = P[i * SW + j];
-                if (q != INT_MAX) {
-                    const uint32_t fi = P[i * SW + cc];
-                    if (fi != 0u) {
-                        x = mont_mul2add(h, x, f.p - fi, P[q * SW + j], f);
-                        P[i * SW + j] = x;
-                    }
+            if (js < nc) {
+                const int j = cc + 1 + js;
+                const bool has = q != INT_MAX;
+                const uint32_t h = has ? P[q * SW + cc] : 0u;
+                const uint32_t pv = has ? P[q * SW + j] : 0u;
+                uint32_t x[U1], fi[U1];
+#pragma unroll
+                for (int u = 0; u < U1; ++u) {
+                    const int i = rg + u * RG1;
+                    x[u] = P[i * SW + j];
+                    fi[u] = P[i * SW + cc];
                 }
-                if (j == cc + 1 && x != 0u && i < cand) cand = i;
+#pragma unroll
+                for (int u = 0; u < U1; ++u) {
+                    const uint32_t xn = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
+                    const bool upd = has && fi[u] != 0u && !((pmask >> u) & 1u);
+                    if (upd) P[(rg + u * RG1) * SW + j] = xn;
+                    x[u] = upd ? xn : x[u];
+                }
+                if (js == 0) {
+                    uint32_t nz = 0u;
+#pragma unroll
+                    for (int u = 0; u < U1; ++u) nz |= x[u] != 0u ? (1u << u) : 0u;
+                    nz &= ~pmask;
+                    if (nz != 0u) cand = rg + (__ffs((int)nz) - 1) * RG1;
+                }
             }
             q = block_min(cand);
         }
