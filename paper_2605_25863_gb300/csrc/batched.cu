@@ -223,21 +223,23 @@ struct BtFold {
 // the pivot flags of its own rows in one register.
 //
 // Only the first WT threads of the block take part (their own barrier when
-// WT is below the block size).
+// WT is below the block size).  WROWS bounds the rows: w + BT_WINDOW for the
+// search, NB for the k <= NB pivot rows of shared-pattern mode, whose smaller
+// padded slab saves the search window's extra row batch.
 //
 // Returns the number of pivots k, or -1 in forced mode when a given pivot
 // vanished.  Unless forced mode, k == w or keep != 0, E is not needed and is
 // not formed; otherwise Et[u * NB + t] = balanced E[t][u] for t, u < k
 // rounded up to 4, zero padded.  Fills sm.J, sm.Pi, sm.own (search) and
 // sm.hs[t] = H_t (held form).
-template <int NB, int WT = BT_THREADS>
+template <int NB, int WT = BT_THREADS, int WROWS = bt_win_rows(NB)>
 __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int64_t ld, int r, int c0, int w, int rows,
                             int forced, int keep, const Field& f, uint32_t* __restrict__ G,
                             BtSmall<NB>& sm, int32_t* __restrict__ Et) {
     constexpr int SWG = 2 * NB + 1;
     constexpr int CW = NB;                  // column slots
     constexpr int RGN = WT / CW;            // row groups
-    constexpr int UMAX = (bt_win_rows(NB) + RGN - 1) / RGN;
+    constexpr int UMAX = (WROWS + RGN - 1) / RGN;
     constexpr int U = UMAX <= 10 ? UMAX : 6;   // rows per batch of independent updates
     static_assert(WT % CW == 0, "column slots must divide the block");
     static_assert(UMAX <= 32, "the pivot flags of a thread's rows fit one word");
@@ -245,7 +247,7 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
     const int cp = tid % CW, rg = tid / CW;
     // load: the panel entries in Montgomery form, coefficients zero; up to 8
     // loads of a thread in flight at once
-    constexpr int LPT = (bt_win_rows(NB) * NB + WT - 1) / WT;
+    constexpr int LPT = (WROWS * NB + WT - 1) / WT;
     constexpr int LB = LPT < 8 ? LPT : 8;
     constexpr int PR = RGN * UMAX;   // slab rows: the rows beyond `rows` hold zeros and stay zero
     static_assert((size_t)PR * SWG * 4 <= bt_win_bytes(NB), "the padded slab fits its region");
@@ -550,7 +552,7 @@ __device__ __forceinline__ bool bt_reduce(uint32_t* __restrict__ A, int m, int n
             }
             if (tid == 0) sm.s_fail = 0;
             __syncthreads();
-            if (bt_window_gj<NB>(A, ld, r, c0, w, k, 1, 1, f, P, sm, Et) < 0) return false;
+            if (bt_window_gj<NB, BT_THREADS, NB>(A, ld, r, c0, w, k, 1, 1, f, P, sm, Et) < 0) return false;
         }
         if (k == 0) continue;
         // kp = k rounded up to 4 (E^T and the tiles are zero padded to it)
