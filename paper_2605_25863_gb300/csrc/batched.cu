@@ -3,15 +3,17 @@
 //
 // Per system the block runs the same blocked Gauss-Jordan elimination as the
 // dense driver (paper section 3.2, blocked by panels of NB columns):
-//   panel    fraction-free elimination of the panel columns of the rows not
-//            yet used (shared memory), recording pivot rows, pivot columns and
-//            multipliers -- or, in shared-pattern mode, the pivot rows and
-//            columns of a probe system and an elimination of the k pivot rows
-//            only;
-//   inverses batched inverses of the k pivot heads;
-//   E        the k x k matrix E = G^{-1} (G = the pivot rows at the pivot
-//            columns), obtained by running the panel's fraction-free
-//            recurrence, the scaling and the back substitution on the identity;
+//   panel    the pivot window (bt_window_gj): fraction-free Gauss-Jordan
+//            elimination of the panel columns of the first w + 8 rows not yet
+//            used, with each row's coefficients over the pivot rows, in shared
+//            memory; it records the pivot rows and columns and yields
+//            E = G^{-1} (G = the pivot rows at the pivot columns) with one
+//            inverse per panel.  In shared-pattern mode the window holds the
+//            probe's k pivot rows only.  When the window lacks a pivot for a
+//            column that a row below it has, a full-height search eliminates
+//            all remaining rows, and E then comes from batched inverses of
+//            the heads and the panel's recurrence, scaling and back
+//            substitution replayed on the identity;
 //   tiles    for each 64-column tile right of the panel start: R = E W (W the
 //            pivot rows' tile), move the displaced rows, and update every
 //            other row: A[d] <- A[d] - F[d] R with lazy signed 64-bit
