@@ -617,24 +617,49 @@ einv_kernel(const DenseState* __restrict__ st, const uint32_t* __restrict__ pane
     __syncthreads();
     for (int t = tid; t < k; t += blockDim.x) hinv[t] = to_mont(hinv[t], f);
     __syncthreads();
+    // Each step updates rows of the block's C columns; thread tid owns column
+    // c = tid % C and the rows RGE apart from its row group tg = tid / C, a
+    // fixed layout with no division per element.  Every product is computed
+    // and the store is skipped where the coefficient is zero, as the
+    // recurrence prescribes, so a thread's rows are independent chains.
+    constexpr int RGE = 256 / C;                      // row groups
+    constexpr int UE = (NB_MAX + RGE - 1) / RGE;      // rows per thread and step
+    static_assert(256 % C == 0, "einv layout");
+    const int cc = tid % C, tg = tid / C;
     // forward (all stages: row j itself is rescaled by h_s at every earlier
     // stage s whose multiplier f_js is nonzero, so E[j][j] changes before s = j)
     for (int s = 0; s + 1 < k; ++s) {
         const uint32_t h = hs[s];
-        for (int e = tid; e < (k - 1 - s) * C; e += blockDim.x) {
-            const int t = s + 1 + e / C, c = e % C;
-            const uint32_t fts = Co[t * S + s];
-            if (fts) Ec[t * C + c] = mont_mul2add(h, Ec[t * C + c], f.p - fts, Ec[s * C + c], f);
+        const uint32_t es = Ec[s * C + cc];
+        uint32_t x[UE], ft[UE];
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+            const int t = s + 1 + tg + u * RGE;
+            ft[u] = t < k ? Co[t * S + s] : 0u;
+            x[u] = t < k ? Ec[t * C + cc] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+            const uint32_t xn = mont_mul2add(h, x[u], f.p - ft[u], es, f);
+            if (ft[u] != 0u) Ec[(s + 1 + tg + u * RGE) * C + cc] = xn;
         }
         __syncthreads();
     }
     for (int e = tid; e < k * C; e += blockDim.x) Ec[e] = mont_mul(Ec[e], hinv[e / C], f);
     __syncthreads();
     for (int s = k - 1; s >= 1; --s) {
-        for (int e = tid; e < s * C; e += blockDim.x) {
-            const int t = e / C, c = e % C;
-            const uint32_t cts = Co[t * S + s];
-            if (cts) Ec[t * C + c] = submod(Ec[t * C + c], mont_mul(cts, Ec[s * C + c], f), f);
+        const uint32_t es = Ec[s * C + cc];
+        uint32_t x[UE], ct[UE];
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+            const int t = tg + u * RGE;
+            ct[u] = t < s ? Co[t * S + s] : 0u;
+            x[u] = t < s ? Ec[t * C + cc] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < UE; ++u) {
+            const uint32_t xn = submod(x[u], mont_mul(ct[u], es, f), f);
+            if (ct[u] != 0u) Ec[(tg + u * RGE) * C + cc] = xn;
         }
         __syncthreads();
     }
