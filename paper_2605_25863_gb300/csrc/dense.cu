@@ -121,18 +121,21 @@ __device__ __forceinline__ int panel_block_min(int v, int* red, int* out) {
 //
 // One cluster of WIN_CTAS blocks: block c holds window rows
 // [c WIN_ROWS_CTA, (c+1) WIN_ROWS_CTA) in its shared memory (Montgomery
-// form, as in panel_kernel).  Per column each block posts its lowest
-// candidate row, one cluster barrier makes the posts (and every block's
-// earlier row updates) visible, every block takes the minimum, reads the
-// pivot row from its owner's shared memory and eliminates its own rows.  A
-// post slot is reused two columns later, after another cluster barrier.
+// form, as in panel_kernel).  Per column each block writes its lowest
+// candidate row's index and its entries from the current column on into
+// every block's shared memory (distributed shared memory stores), one
+// cluster barrier makes them (and every block's earlier row updates)
+// visible, and every block takes the minimum and eliminates its own rows
+// with the winning row read locally.  A slot is reused two columns later,
+// after another cluster barrier.
 __global__ void __cluster_dims__(WIN_CTAS, 1, 1) __launch_bounds__(WIN_THREADS)
 window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int w, Field f, DenseState* st,
               uint32_t* __restrict__ panelU, int G, const int32_t* __restrict__ rowmap) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     __shared__ __align__(16) uint32_t P[WIN_ROWS_CTA * (NB_MAX + 1)];
-    __shared__ int post[2];
+    __shared__ int posts[2][WIN_CTAS];                          // posts[par][b]: block b's candidate row
+    __shared__ __align__(16) uint32_t cbuf[2][WIN_CTAS][NB_MAX];  // cbuf[par][b][j]: that row at column cc + j
     __shared__ int red[WIN_THREADS / 32];
     __shared__ unsigned char isp[WIN_ROWS_CTA];
     __shared__ int own[NB_MAX], Jc[NB_MAX];        // window row and panel column of pivot t
@@ -155,25 +158,36 @@ window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int
     const int jj = tid % NB_MAX, rg = tid / NB_MAX;
     for (int cc = 0; cc < w; ++cc) {
         // this block's lowest remaining row with a nonzero entry in column cc
-        int cand = (tid < lrows && !isp[tid] && P[tid * SW + cc] != 0u) ? g0 + tid : INT_MAX;
+        int cand = (tid < lrows && !isp[tid] && P[tid * SW + cc] != 0u) ? tid : INT_MAX;
         cand = __reduce_min_sync(0xffffffffu, cand);
         if (lane == 0) red[warp] = cand;
         __syncthreads();
-        if (tid == 0) {
-            int v = INT_MAX;
+        int v = INT_MAX;   // this block's lowest candidate row (local index)
 #pragma unroll
-            for (int x = 0; x < WIN_THREADS / 32; ++x) v = min(v, red[x]);
-            post[par] = v;
+        for (int x = 0; x < WIN_THREADS / 32; ++x) v = min(v, red[x]);
+        // push the post and the candidate row's entries from column cc on into
+        // every block of the cluster, so that after the barrier the pivot row
+        // is read from local shared memory; the slots alternate by column
+        // parity, and a slot is rewritten two columns later, after the next
+        // barrier, when every block has finished reading it
+        const int nrem = w - cc;
+        if (tid < WIN_CTAS) *cluster.map_shared_rank(&posts[par][c], tid) = v == INT_MAX ? INT_MAX : g0 + v;
+        if (v != INT_MAX) {
+            for (int e = tid; e < WIN_CTAS * nrem; e += WIN_THREADS) {
+                const int b = e % WIN_CTAS, j = e / WIN_CTAS;
+                cluster.map_shared_rank(&cbuf[par][c][0], b)[j] = P[v * SW + cc + j];
+            }
         }
-        cluster.sync();   // posts and every block's row updates of column cc - 1 are visible
+        cluster.sync();   // posts, pushed rows and every block's row updates of column cc - 1 are visible
         int q = INT_MAX;
 #pragma unroll
-        for (int b = 0; b < WIN_CTAS; ++b) q = min(q, *cluster.map_shared_rank(&post[par], b));
+        for (int b = 0; b < WIN_CTAS; ++b) q = min(q, posts[par][b]);
+        const int pc = par;
         par ^= 1;
         if (q == INT_MAX) continue;   // no pivot in this column (the same in every block)
         const int owner = q / WIN_ROWS_CTA, ql = q - owner * WIN_ROWS_CTA;
-        const uint32_t* prow = cluster.map_shared_rank(P, owner) + ql * SW;
-        const uint32_t h = prow[cc];
+        const uint32_t* prow = &cbuf[pc][owner][0];   // prow[j - cc] = pivot row at column j >= cc
+        const uint32_t h = prow[0];
         if (owner == c && tid == 0) isp[ql] = 1;
         if (tid == 0) {
             own[kk] = q;
@@ -186,7 +200,7 @@ window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int
         if (jj < nc) {
             constexpr int U = (WIN_ROWS_CTA + RG - 1) / RG;
             const int j = cc + 1 + jj;
-            const uint32_t pv = prow[j];
+            const uint32_t pv = prow[j - cc];
             uint32_t fi[U], x[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -195,12 +209,13 @@ window_kernel(const uint32_t* __restrict__ M, int64_t m, int64_t ld, int c0, int
                 fi[u] = ok ? P[i * SW + cc] : 0u;
                 x[u] = ok ? P[i * SW + j] : 0u;
             }
+            // every product computed, stored where f_i != 0: the rows'
+            // chains interleave
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (fi[u] != 0u) x[u] = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (fi[u] != 0u) P[(rg + u * RG) * SW + j] = x[u];
+            for (int u = 0; u < U; ++u) {
+                const uint32_t xn = mont_mul2add(h, x[u], f.p - fi[u], pv, f);
+                if (fi[u] != 0u) P[(rg + u * RG) * SW + j] = xn;
+            }
         }
         __syncthreads();
     }
