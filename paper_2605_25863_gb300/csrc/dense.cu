@@ -25,8 +25,11 @@
 //      kernel is the k reduced pivot rows (identity at J).
 //   5. move_kernel    rows of [r, r+k) that are not pivots move to the pivot
 //      rows' old places (the paper's row swap, done once per panel).
-//   6. update_plain   every row d outside [r, r+k):  M[d, c0:n] -= F[d] * R
-//      (mod p), the O(n^3) trailing update; rows r..r+k-1 receive R.
+//   6. the update     every row d outside [r, r+k):  M[d, c0:n] -= F[d] * R
+//      (mod p), the O(n^3) trailing update; rows r..r+k-1 receive R.  On
+//      CUDA cores (update_plain), on the integer tensor pipe (update_limb,
+//      update_crt), or on both at once (update_hybrid), as the path option
+//      or the matrix size selects.
 //   7. finish_kernel  appends J to the pivot list and advances r by k.
 //
 // Because R is fully reduced (identity at the pivot columns), the update
