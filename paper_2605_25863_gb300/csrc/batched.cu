@@ -394,8 +394,8 @@ __device__ __forceinline__ int bt_window_gj(const uint32_t* __restrict__ A, int6
 // all balanced residues (YBAL: Y holds raw residues, balanced on the fly).
 // The loop is unrolled by the fold cadence FOLD, so the folds sit at fixed
 // places and the shared-memory reads of a group issue together; the last
-// k mod FOLD products need no fold before the final reduction (fewer than
-// FOLD products after a fold keep the accumulator bound).
+// group or the last k mod FOLD products need no fold before the final
+// reduction (at most FOLD products after a fold keep |acc| < 2^63).
 template <int FOLD, int MR, int SH, bool YBAL>
 __device__ __forceinline__ void bt_kloop(int64_t (&acc)[MR][4], const int32_t* __restrict__ X, int ldx,
                                          const int32_t* __restrict__ Y, int ldy, int k, const Field& f,
@@ -425,14 +425,23 @@ __device__ __forceinline__ void bt_kloop(int64_t (&acc)[MR][4], const int32_t* _
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] += (int64_t)xa[a] * yb[b];
     };
+    // groups of FOLD products, each followed by a fold, except the last group
+    // when no product follows it (FOLD products after a fold stay below
+    // 2^63, which the final reduction accepts)
     const int kf = k - k % FOLD;
-    for (int t0 = 0; t0 < kf; t0 += FOLD) {
+    const int kfold = k % FOLD == 0 ? kf - FOLD : kf;   // groups before kfold are folded
+    int t0 = 0;
+    for (; t0 < kfold; t0 += FOLD) {
 #pragma unroll
         for (int tt = 0; tt < FOLD; ++tt) step(t0 + tt);
 #pragma unroll
         for (int a = 0; a < MR; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = fold_any<SH>(acc[a][b], f, fs);
+    }
+    if (t0 < kf) {
+#pragma unroll
+        for (int tt = 0; tt < FOLD; ++tt) step(t0 + tt);
     }
     for (int t = kf; t < k; ++t) step(t);
 }
