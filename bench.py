@@ -55,7 +55,7 @@ IMAD_WIDE_PER_SM_CLK = 32
 # (ncu: 1.627 + 1.875 GB and 0.024 + 0.0002 GB read + written by the two
 # launches of the 2000-system uneven batch, whose matrices hold 0.385 GB;
 # summary in profiles/batched_uneven_bucket512.md)
-BATCHED_DRAM_PER_MATRIX_BYTE = 3.325e9 / 0.3854e9
+BATCHED_DRAM_PER_MATRIX_BYTE = 3.358e9 / 0.3854e9
 
 # DRAM bytes per output of the update kernels from one ncu capture each
 # (dram__bytes_read.sum + dram__bytes_write.sum of one panel's update in the
