@@ -128,6 +128,31 @@ def test_shared_pattern_fallbacks():
         assert st[s] == 0
 
 
+@pytest.mark.parametrize("widths", [[16, 16, 16, 16, 16], [64, 64, 64, 32, 32]])
+def test_every_panel_width_matches_oracle(widths):
+    """Every panel width the kernel is built for (16, 32 and 64 columns; 64
+    fits systems of at most 256 rows) against the oracle, with the search
+    and with the shared pattern: the pivot window's row batches, the update's
+    4- and 8-row items and the pattern's pivot-row slab differ by width.  The
+    widths are set explicitly, as a caller may, and restored afterwards."""
+    saved = linac.linac_batched_panel_widths()
+    try:
+        linac.linac_batched_set_panel_widths(widths)
+        assert linac.linac_batched_panel_widths() == widths
+        B = synth.batched_uneven(count=60, lo=4, hi=1000, seed=33, deficient_frac=0.3)
+        out, ranks, piv, poff, st = run_batched(B, B.p)
+        check_all(B, B.p, out, ranks, piv, poff)
+        assert (ranks == B.nA - B.deficiency).all()
+        # a 240 x 256 template: systems of the 256-row bucket, reduced with
+        # the shared pattern at that bucket's width
+        Bs = synth.shared_pattern(count=24, rows=240, cols=256, rhs=16)
+        out, ranks, piv, poff, st = run_batched(Bs, Bs.p, flags=linac.LINAC_SHARED_PATTERN)
+        check_all(Bs, Bs.p, out, ranks, piv, poff)
+        assert (ranks == 240).all() and (st == 0).all()
+    finally:
+        linac.linac_batched_set_panel_widths(saved)
+
+
 def test_workload_shared_pattern_4096_sampled():
     B = synth.shared_pattern(count=4096)
     out, ranks, piv, poff, st = run_batched(B, B.p, flags=linac.LINAC_SHARED_PATTERN)
